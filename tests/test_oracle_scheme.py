@@ -1,0 +1,235 @@
+"""Scheme-level pins of the oracle: conservation, free-stream preservation, symmetries,
+Euler eigenvectors, and accuracy against exact solutions and the paper's printed tables.
+
+Printed values used (HWENO-U rows):
+  Table 3.1 (Example 3.1, 1D Burgers, T = 0.5/pi): N=120 Linf 2.99E-07 L1 2.51E-08;
+            N=160 Linf 7.13E-08 L1 5.43E-09
+  Table 3.2 (first moment):   N=120 Linf 1.18E-07;  N=160 Linf 2.72E-08
+  Table 3.3 (Example 3.2, 1D Euler density wave, T = 2): N=80 L1 8.08E-09; N=120 L1 1.04E-09
+The paper does not state the time step of these runs.  The tables are reproduced with a
+time step small enough for the spatial error to dominate (dt = 0.05 dx for Burgers,
+0.01 dx for Euler); see also tests/golden/paper_tables.json.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2402_03074_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------------------------------
+def test_advection_error_matches_rk3_amplitude_closed_form():
+    """u_t + u_x = 0, N = 200, CFL 0.6, T = 2: the error is the SSP-RK3 amplitude/phase error
+    of the single Fourier mode, |R(-i theta)^n R(-i theta_last) e^{i pi T} - 1| with
+    R(z) = 1 + z + z^2/2 + z^3/6 (the spatial error is orders of magnitude smaller)."""
+    w = I.advection_sine_1d(200)
+    P = O.Problem(dim=1, eq=O.ADVECTION, nx=200, x0=0.0, x1=2.0, ax=1.0)
+    U, t, ns, st = O.run(P, w.U0, 0.0, 2.0)
+    assert st == 0 and t == 2.0 and ns == 334
+    err = np.abs(U[0, 0] - I.advection_exact_1d(200, 2.0)[0, 0]).max()
+    dt = 0.6 * 0.01
+    R = lambda z: 1 + z + z * z / 2 + z ** 3 / 6
+    nfull = int(round(2.0 / dt - 0.5))
+    pred = abs(R(-1j * math.pi * dt) ** nfull * R(-1j * math.pi * (2.0 - nfull * dt)) - 1.0)
+    assert err == pytest.approx(pred, rel=0.03)
+
+
+def test_advection_fifth_order():
+    errs = []
+    ns = [40, 80, 160]
+    for n in ns:
+        w = I.advection_sine_1d(n)
+        P = O.Problem(dim=1, eq=O.ADVECTION, nx=n, x0=0.0, x1=2.0, ax=1.0)
+        dt = 0.6 * (2.0 / n) * (40.0 / n) ** (2.0 / 3.0)   # dt ~ dx^(5/3)
+        U, t, _, st = O.run(P, w.U0, 0.0, 2.0, dt_fixed=dt)
+        errs.append(np.abs(U[0, 0] - I.advection_exact_1d(n, 2.0)[0, 0]).mean())
+    order = math.log(errs[1] / errs[2]) / math.log(2.0)
+    assert order > 4.8, errs
+
+
+@pytest.mark.parametrize("n", [120, 160])
+def test_burgers_matches_table_3_1_and_3_2(n):
+    g = _golden()["table_3_1_burgers_1d"][str(n)]
+    gv = _golden()["table_3_2_burgers_1d_first_moment"][str(n)]
+    w = I.burgers_sine_1d(n)
+    P = O.Problem(dim=1, eq=O.BURGERS, nx=n, x0=0.0, x1=2.0)
+    U, t, _, st = O.run(P, w.U0, 0.0, w.t_end, dt_fixed=0.05 * 2.0 / n)
+    ex = I.burgers_exact_1d(n, w.t_end)
+    e = U[0, 0] - ex[0, 0]
+    ev = U[0, 1] - ex[0, 1]
+    assert np.abs(e).max() == pytest.approx(g["linf"], rel=0.05)
+    assert np.abs(e).mean() == pytest.approx(g["l1"], rel=0.12)
+    assert np.abs(ev).max() == pytest.approx(gv["linf"], rel=0.16)
+
+
+@pytest.mark.parametrize("n", [80, 120])
+def test_euler_density_wave_matches_table_3_3(n):
+    g = _golden()["table_3_3_euler_1d"][str(n)]
+    w = I.euler_density_wave_1d(n)
+    P = O.Problem(dim=1, eq=O.EULER, nx=n, x0=0.0, x1=2.0)
+    U, t, _, st = O.run(P, w.U0, 0.0, 2.0, dt_fixed=0.01 * 2.0 / n)
+    e = U[0, 0] - I.euler_density_wave_exact_1d(n, 2.0)[0, 0]
+    assert np.abs(e).mean() == pytest.approx(g["l1"], rel=0.3)
+    assert g["linf"] / 2.0 < np.abs(e).max() < 2.0 * g["linf"]
+
+
+def test_2d_linear_weights_fifth_order():
+    errs = []
+    for n in (16, 32):
+        w = I.advection_sine_2d(n, t_end=0.5)
+        P = O.Problem(dim=2, eq=O.ADVECTION, nx=n, ny=n, x0=0, x1=4, y0=0, y1=4, weights=O.W_LINEAR)
+        U, _, _, _ = O.run(P, w.U0, 0.0, 0.5, dt_fixed=0.02 * 4.0 / n)
+        ex = I.moments_2d(lambda x, y: 0.5 + np.sin(np.pi * (x + y - 1.0) / 2), 0, 4, 0, 4, n, n)
+        errs.append(np.abs(U[0, 0] - ex[0, 0]).mean())
+    assert math.log(errs[0] / errs[1]) / math.log(2.0) > 4.8
+
+
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["adv1d", "burg1d", "eul1d", "burg2d", "eul2d"])
+def test_conservation_periodic(case):
+    rng = np.random.default_rng(5)
+    if case.endswith("1d"):
+        eq = {"adv1d": O.ADVECTION, "burg1d": O.BURGERS, "eul1d": O.EULER}[case]
+        P = O.Problem(dim=1, eq=eq, nx=37, x0=0.0, x1=1.0)
+        U = I.random_state(P.shape, 3, eq=eq)
+        steps = 10
+    else:
+        eq = {"burg2d": O.BURGERS, "eul2d": O.EULER}[case]
+        P = O.Problem(dim=2, eq=eq, nx=11, ny=9, x0=0, x1=1, y0=0, y1=1)
+        U = I.random_state(P.shape, 4, eq=eq)
+        steps = 3
+    s0 = U[:, 0].sum(axis=(1, 2))
+    V, t, ns, st = O.run(P, U, 0.0, 1e9, max_steps=steps)
+    assert st == 0 and ns == steps
+    s1 = V[:, 0].sum(axis=(1, 2))
+    scale = np.abs(U[:, 0]).sum(axis=(1, 2))
+    assert (np.abs(s1 - s0) <= 1e-14 * scale).all(), (s1 - s0) / scale
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_free_stream_preserved(dim):
+    if dim == 1:
+        P = O.Problem(dim=1, eq=O.EULER, nx=12, bc=(O.BC_TRANSMISSIVE,) * 4)
+        U = np.zeros(P.shape)
+        U[:, 0] = np.array([1.3, 0.7, 2.9])[:, None, None]
+    else:
+        P = O.Problem(dim=2, eq=O.EULER, nx=7, ny=6, bc=(O.BC_TRANSMISSIVE,) * 4)
+        U = np.zeros(P.shape)
+        U[:, 0] = np.array([1.3, 0.7, -0.4, 2.9])[:, None, None]
+    V, _, _, st = O.run(P, U, 0.0, 1e9, max_steps=3)
+    assert st == 0
+    np.testing.assert_allclose(V, U, rtol=0, atol=1e-14)
+
+
+def test_mirror_symmetry_1d_euler():
+    P = O.Problem(dim=1, eq=O.EULER, nx=24, x0=-1.0, x1=1.0, bc=(O.BC_TRANSMISSIVE,) * 4)
+    U = I.random_state(P.shape, 8, eq=O.EULER)
+    M = U[:, :, :, ::-1].copy()
+    M[:, 1] *= -1.0          # first moments change sign under x -> -x
+    M[1] *= -1.0             # momentum changes sign
+    A, _, _, _ = O.run(P, U, 0.0, 1e9, max_steps=4)
+    B, _, _, _ = O.run(P, M, 0.0, 1e9, max_steps=4)
+    Bm = B[:, :, :, ::-1].copy()
+    Bm[:, 1] *= -1.0
+    Bm[1] *= -1.0
+    np.testing.assert_allclose(Bm, A, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("eq", [O.BURGERS, O.EULER])
+def test_transpose_symmetry_2d(eq):
+    P = O.Problem(dim=2, eq=eq, nx=10, ny=10, bc=(O.BC_TRANSMISSIVE,) * 4)
+    U = I.random_state(P.shape, 9, eq=eq)
+    T = U.transpose(0, 1, 3, 2)[:, [0, 2, 1]].copy()
+    if eq == O.EULER:
+        T = T[[0, 2, 1, 3]].copy()
+    A, _, _, _ = O.run(P, U, 0.0, 1e9, max_steps=2)
+    B, _, _, _ = O.run(P, T, 0.0, 1e9, max_steps=2)
+    Bt = B.transpose(0, 1, 3, 2)[:, [0, 2, 1]]
+    if eq == O.EULER:
+        Bt = Bt[[0, 2, 1, 3]]
+    np.testing.assert_allclose(Bt, A, rtol=0, atol=1e-13)
+
+
+def test_reflective_wall_equals_mirrored_periodic_domain():
+    """A reflective wall at both ends equals the periodic doubled domain with mirrored data."""
+    n = 16
+    P = O.Problem(dim=1, eq=O.EULER, nx=n, x0=0.0, x1=1.0, bc=(O.BC_REFLECTIVE,) * 4)
+    U = I.random_state(P.shape, 11, eq=O.EULER)
+    M = U[:, :, :, ::-1].copy()
+    M[:, 1] *= -1.0
+    M[1] *= -1.0
+    D = np.concatenate([M, U], axis=3)
+    PD = O.Problem(dim=1, eq=O.EULER, nx=2 * n, x0=-1.0, x1=1.0, bc=(O.BC_PERIODIC,) * 4)
+    A, _, _, _ = O.run(P, U, 0.0, 1e9, max_steps=3)
+    B, _, _, _ = O.run(PD, D, 0.0, 1e9, max_steps=3)
+    np.testing.assert_allclose(B[:, :, :, n:], A, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------------------------------------
+def _euler_flux(u, gam, dim, d):
+    """Textbook Euler flux (complex-safe), independent of the oracle."""
+    if dim == 1:
+        rho, m, E = u
+        v = m / rho
+        p = (gam - 1) * (E - 0.5 * m * v)
+        return np.array([m, m * v + p, v * (E + p)])
+    rho, mx, my, E = u
+    vx, vy = mx / rho, my / rho
+    p = (gam - 1) * (E - 0.5 * (mx * vx + my * vy))
+    if d == 0:
+        return np.array([mx, mx * vx + p, my * vx, vx * (E + p)])
+    return np.array([my, mx * vy, my * vy + p, vy * (E + p)])
+
+
+@pytest.mark.parametrize("dim,d", [(1, 0), (2, 0), (2, 1)])
+def test_euler_eigenvectors(dim, d):
+    """R diagonalises the flux Jacobian (complex-step derivative) and L = R^-1."""
+    P = O.Problem(dim=dim, eq=O.EULER)
+    rng = np.random.default_rng(dim * 10 + d)
+    for _ in range(5):
+        rho, p = rng.uniform(0.3, 3.0, size=2)
+        vel = rng.uniform(-2, 2, size=dim)
+        u = I.euler_conserved(rho, vel[0], p, v=(vel[1] if dim == 2 else None))
+        R, L = O.eigen(P, u, d)
+        n = len(u)
+        J = np.zeros((n, n))
+        for k in range(n):
+            du = u.astype(complex)
+            du[k] += 1e-30j
+            J[:, k] = _euler_flux(du, 1.4, dim, d).imag / 1e-30
+        Lam = L @ J @ R
+        np.testing.assert_allclose(Lam - np.diag(np.diag(Lam)), 0.0, atol=1e-12)
+        c = math.sqrt(1.4 * p / rho)
+        lam = sorted(np.diag(Lam))
+        expect = sorted([vel[d] - c, vel[d], vel[d] + c] + ([vel[d]] if dim == 2 else []))
+        np.testing.assert_allclose(lam, expect, atol=1e-12)
+        np.testing.assert_allclose(L @ R, np.eye(n), atol=1e-13)
+
+
+def test_stage_cells_equals_full_stage():
+    """The sampled-cell evaluation gives bitwise the values of the whole-grid stage."""
+    for (dim, eq, nx, ny) in [(1, O.EULER, 20, 1), (2, O.EULER, 9, 7), (2, O.BURGERS, 8, 5)]:
+        P = O.Problem(dim=dim, eq=eq, nx=nx, ny=ny, bc=(O.BC_TRANSMISSIVE,) * 4)
+        U = I.random_state(P.shape, 2, eq=eq)
+        a = O.alpha(P, U)
+        for k in (1, 2):
+            Vh = None if k == 1 else np.random.default_rng(0).normal(size=(P.ncomp, P.nmom - 1, ny, nx))
+            full, vh, _ = O.stage(P, k, U, U, Vh, a, 1e-3)
+            cells = np.array([0, nx - 1, nx * ny - 1, (ny // 2) * nx + nx // 2])
+            out, vho, _ = O.stage_cells(P, k, U, U, Vh, a, 1e-3, cells)
+            for s, q in enumerate(cells):
+                j, i = divmod(int(q), nx)
+                np.testing.assert_array_equal(out[s], full[:, :, j, i])
+                if k == 1:
+                    np.testing.assert_array_equal(vho[s], vh[:, :, j, i])
