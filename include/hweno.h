@@ -1,0 +1,171 @@
+/*
+ * hweno.h -- C ABI of the GB300 (sm_103a) HWENO-U library.
+ *
+ * The library advances the zeroth and first moments of the cells of a uniform 1D or 2D
+ * grid with the fifth-order HWENO-U scheme of Fan, Qiu and Zhao (arXiv 2402.03074):
+ * Hermite reconstruction on the compact 3-cell / 3x3-cell stencil (Sec. 2.1 Steps 1-3,
+ * Sec. 2.2 Steps 1-3, Appendix), scale-invariant nonlinear weights (Eq. 2.11, 2.22),
+ * global Lax-Friedrichs fluxes (Eq. 2.4 and its 2D form), the moment equations (Eq. 2.3,
+ * 2.16), the first-moment modification v-hat / w-hat (Eq. 2.12, 2.23) and the modified
+ * SSP-RK3 (Eq. 2.13), for u_t + f(u)_x (+ g(u)_y) = 0 with f, g linear advection, Burgers
+ * (u^2/2) or the Euler equations of a gamma-law gas (local characteristic decomposition,
+ * Remark 2.2).  Every step of the scheme runs in CUDA kernels on the GPU; there is no CPU
+ * fallback: without a usable device hweno_create returns HWENO_ERR_CUDA.
+ *
+ * Conventions
+ *   - Every function returns an int status: 0 = HWENO_OK, > 0 = HWENO_PENDING,
+ *     < 0 = an error (below).  No function aborts or exits the process.
+ *   - Host moment layout (all host buffers, caller-owned):
+ *         double U[NC][NM][ny][nx]      (x fastest; ny = 1 in 1D)
+ *     NC = 1 for scalar laws, 3 for 1D Euler (rho, rho*u, E), 4 for 2D Euler
+ *     (rho, rho*u, rho*v, E); NM = 2 in 1D (average, x first moment), 3 in 2D
+ *     (average, x first moment, y first moment).  The first moments are
+ *     (1/|I|) int u (x - x_i)/dx and (1/|I|) int u (y - y_j)/dy (Eq. 2.2, 2.15).
+ *   - The engine owns all device memory it allocates; the caller owns every host buffer
+ *     and every device buffer it passes to the hweno_stage_device entry point.
+ *   - One engine may be used from several host threads; calls are serialised internally.
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HWENO_OK 0
+#define HWENO_PENDING 1
+#define HWENO_ERR_ARG (-1)         /* invalid argument or unknown id / ticket */
+#define HWENO_ERR_OOM (-2)         /* device allocation failed */
+#define HWENO_ERR_CUDA (-3)        /* CUDA runtime error or no usable device */
+#define HWENO_ERR_NONPHYSICAL (-4) /* rho <= 0, p <= 0 or a non-finite value appeared */
+#define HWENO_ERR_BUSY (-5)        /* over the memory budget or the slot table is full */
+#define HWENO_ERR_TIMEOUT (-6)     /* a bounded wait expired */
+#define HWENO_ERR_STATE (-7)       /* call out of order (e.g. poll of a retired ticket) */
+
+/* equations: f = a_x u, g = a_y u | f = g = u^2/2 | Euler, gamma-law gas */
+#define HWENO_ADVECTION 0
+#define HWENO_BURGERS 1
+#define HWENO_EULER 2
+/* boundary conditions, per side (x-left, x-right, y-bottom, y-top):
+   periodic; transmissive (ghost cells copy the moments of the nearest interior cell);
+   reflective (mirror cell, normal momentum and normal first moments negated) */
+#define HWENO_BC_PERIODIC 0
+#define HWENO_BC_TRANSMISSIVE 1
+#define HWENO_BC_REFLECTIVE 2
+/* arithmetic: all FP64, or FP32 reconstruction / flux / limiter arithmetic with FP64
+   smoothness indicators, nonlinear weights, stage combination, sums and dt */
+#define HWENO_FP64 0
+#define HWENO_MIXED32 1
+/* nonlinear weights: scale-invariant (Eq. 2.11 / 2.22) or the original ones with
+   u_ave = 1 (the Remark after Eq. 2.11) */
+#define HWENO_W_SCALE_INVARIANT 0
+#define HWENO_W_ORIGINAL 1
+
+/* A problem u_t + f(u)_x (+ g(u)_y) = 0 on [x0,x1] (x [y0,y1]) (Sec. 2.1, 2.2). */
+typedef struct hweno_problem {
+  int dim;            /* 1 or 2 */
+  int equation;       /* HWENO_ADVECTION | HWENO_BURGERS | HWENO_EULER */
+  int nx, ny;         /* cells (ny = 1 in 1D); 2D needs dx == dy (square cells, Eq. 2.20) */
+  double x0, x1, y0, y1;
+  double ax, ay;      /* advection speeds */
+  double gamma;       /* ratio of specific heats (Euler), e.g. 1.4 */
+  int bc[4];          /* HWENO_BC_* for x-left, x-right, y-bottom, y-top */
+  double cfl;         /* dt = cfl*dx/alpha (1D), cfl/(alpha1/dx + alpha2/dy) (2D); 0.6 */
+  double dt_fixed;    /* > 0: use this time step instead of the CFL rule */
+  double t_end;       /* end time used by hweno_submit */
+  int precision;      /* HWENO_FP64 | HWENO_MIXED32 */
+  int characteristic; /* Euler: 1 = local characteristic decomposition (Remark 2.2) */
+  int weights;        /* HWENO_W_SCALE_INVARIANT | HWENO_W_ORIGINAL */
+  double gamma_lo;    /* linear weight of each low-degree polynomial (1/400, Sec. 3) */
+  double eps;         /* epsilon of the nonlinear weights (1e-10, Eq. 2.11); must be > 0 */
+} hweno_problem;
+
+typedef struct hweno_engine_config {
+  int device;               /* CUDA device ordinal */
+  uint64_t hbm_budget_bytes;/* device memory the engine may hold for solves (0: 90% free) */
+  int max_slots;            /* maximum number of live solves (0: 256) */
+  int server_thread;        /* 1: hweno_submit work is advanced by a background thread */
+} hweno_engine_config;
+
+typedef struct hweno_result {
+  int status;               /* HWENO_OK / HWENO_PENDING / error of the solve */
+  double t;                 /* simulated time reached */
+  int64_t steps;            /* time steps taken */
+  double t_arrive, t_admit, t_finish; /* host wall-clock seconds (CLOCK_MONOTONIC) */
+} hweno_result;
+
+typedef struct hweno_engine hweno_engine;
+
+/* Create an engine on cfg->device (NULL: device 0, defaults).  Returns HWENO_ERR_CUDA if the
+   device cannot be used.  *out is NULL on error. */
+int hweno_create(const hweno_engine_config* cfg, hweno_engine** out);
+/* Stop the server thread, free every solve and the engine.  NULL is ignored. */
+void hweno_destroy(hweno_engine* eng);
+/* Message describing the last error on this engine (static storage of the engine). */
+const char* hweno_last_error(const hweno_engine* eng);
+/* The CUDA stream (cudaStream_t) all work of the engine is ordered on; for timing events and
+   interoperation.  The engine keeps ownership. */
+void* hweno_engine_stream(hweno_engine* eng);
+/* Number of conserved components / moments of a problem (0 if the problem is invalid). */
+int hweno_ncomp(const hweno_problem* p);
+int hweno_nmom(const hweno_problem* p);
+
+/* ---- single-solve (synchronous) path ---------------------------------------------- */
+/* Validate the problem, allocate its device state and copy the initial moments in (host
+   layout above).  t starts at 0.  *id identifies the solve on this engine. */
+int hweno_open(hweno_engine* eng, const hweno_problem* p, const double* moments_host,
+               uint64_t* id);
+/* Replace the state and time of a solve (checkpoint restore). */
+int hweno_set_state(hweno_engine* eng, uint64_t id, const double* moments_host, double t);
+/* Copy the moments and the time out (either pointer may be NULL). */
+int hweno_get_state(hweno_engine* eng, uint64_t id, double* moments_host, double* t);
+/* One full SSP-RK3 step (three stages, Eq. 2.13); dt from the CFL rule or dt_fixed.
+   *dt_taken (may be NULL) receives the step.  Returns HWENO_ERR_NONPHYSICAL if the new state
+   has rho <= 0, p <= 0 or non-finite values (the state is kept as computed). */
+int hweno_step(hweno_engine* eng, uint64_t id, double* dt_taken);
+/* Steps until t == t_end (the last step is clipped to land on t_end) or max_steps steps
+   (max_steps < 0: no limit).  The step loop runs as replays of a captured CUDA graph with
+   no host round trip per step; the status word is checked between batches of steps. */
+int hweno_advance(hweno_engine* eng, uint64_t id, double t_end, int64_t max_steps,
+                  int64_t* steps_taken);
+/* Free a solve. */
+int hweno_close(hweno_engine* eng, uint64_t id);
+
+/* ---- served (asynchronous, continuous batching) path -------------------------------- */
+/* Queue a solve to be advanced to p->t_end.  The moments are copied at the call.  Requests
+   are admitted while the memory budget and the slot table allow; all live solves are
+   advanced together, one batched launch per RK stage.  *ticket identifies the request. */
+int hweno_submit(hweno_engine* eng, const hweno_problem* p, const double* moments_host,
+                 uint64_t* ticket);
+/* HWENO_PENDING while the request is queued or running; HWENO_OK once done (moments_out,
+   if not NULL, receives the final moments and the request is retired); an error status if
+   the solve failed.  info (may be NULL) receives the timing record. */
+int hweno_poll(hweno_engine* eng, uint64_t ticket, double* moments_out, hweno_result* info);
+/* Advance the served solves by up to max_steps steps each on the calling thread (when the
+   engine has no server thread).  *active receives the number of live solves. */
+int hweno_serve(hweno_engine* eng, int64_t max_steps, int* active);
+
+/* ---- one stage on caller-owned device buffers (Eq. 2.13, stage k = 1, 2, 3) ---------- */
+/* U_in: stage input, U_n: base state U^n, Vh: first-moment modifications of U^n
+   (NC*(NM-1) arrays of ny*nx doubles; written when k == 1, read when k > 1), U_out: output
+   (may alias U_n, not U_in).  All device pointers, host layout, double.  alpha_in: 2
+   device doubles (LF speeds of U_in per direction); alpha_out: 2 device doubles that the
+   stage raises (atomic max) to the wave speeds of U_out; dt: 1 device double; status: 1
+   device uint32 OR-ed with 1 if U_out is not physical.  stream: cudaStream_t (NULL:
+   legacy default stream).  Asynchronous; returns HWENO_ERR_ARG / HWENO_ERR_CUDA on a bad
+   problem or a launch failure. */
+int hweno_stage_device(const hweno_problem* p, int k, const double* U_in, const double* U_n,
+                       double* Vh, double* U_out, const double* alpha_in, double* alpha_out,
+                       const double* dt, uint32_t* status, void* stream);
+/* Wave speeds of a device state: raises alpha_out[0..1] (device) to max |f'|, |g'|. */
+int hweno_alpha_device(const hweno_problem* p, const double* U, double* alpha_out,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWENO_H */

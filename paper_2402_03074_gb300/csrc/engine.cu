@@ -1,0 +1,629 @@
+// engine.cu -- C ABI of the HWENO-U library: engine, solves, time stepping, served path.
+//
+// Per solve the device holds U^n (U0), the stage outputs U^(1) (U1) and U^(2) (U2), the
+// first-moment modifications of U^n (Vh, Eq. 2.13 needs them in all three stages) and a
+// block of scalars (LF speeds, dt, t, step counters, active flag, status word).  A time
+// step is four launches on the engine stream: the dt kernel (Delta t from the LF speeds of
+// U^n, clipped to t_end; it also clears the speed slots the stages accumulate into) and the
+// three fused stage kernels.  hweno_advance replays a captured CUDA graph of several steps;
+// steps after t_end or the step limit are skipped on the device (active flag), so the host
+// only reads the scalars back between batches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hweno.h"
+#include "hweno_device.cuh"
+#include "launch.h"
+#include "server.h"
+
+namespace hw {
+
+// ------------------------------------------------------------------------------------
+// device scalars of a solve
+struct DevScal {
+  double alpha[4][2];  // [3]: speeds of U^n (from the previous step / open), [0..2]: stage inputs
+  double dt;
+  double t;
+  double t_end;
+  double dt_fixed;
+  double cfl;
+  long long steps;
+  long long step_limit;
+  int active;
+  uint32_t status;
+};
+
+__global__ void dt_kernel(DevScal* s, double inv_dx, double inv_dy, int dim) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double a0 = s->alpha[3][0], a1 = s->alpha[3][1];
+  s->alpha[0][0] = a0;
+  s->alpha[0][1] = a1;
+  s->alpha[1][0] = s->alpha[1][1] = 0.0;
+  s->alpha[2][0] = s->alpha[2][1] = 0.0;
+  s->alpha[3][0] = s->alpha[3][1] = 0.0;
+  const double t = s->t, te = s->t_end;
+  if (!(t < te) || s->steps >= s->step_limit || s->status != 0u) {
+    s->active = 0;
+    s->dt = 0.0;
+    s->alpha[3][0] = a0;  // keep the speeds of the (unchanged) state
+    s->alpha[3][1] = a1;
+    return;
+  }
+  double dt;
+  if (s->dt_fixed > 0.0) {
+    dt = s->dt_fixed;
+  } else {
+    const double rate = a0 * inv_dx + (dim == 2 ? a1 * inv_dy : 0.0);
+    dt = (rate > 0.0) ? s->cfl / rate : te - t;
+  }
+  double tn = t + dt;
+  if (!(tn < te)) {  // clip the last step onto t_end
+    dt = te - t;
+    tn = te;
+  }
+  s->dt = dt;
+  s->t = tn;
+  s->steps += 1;
+  s->active = 1;
+}
+
+// wave speeds of a state: max |f'| and |g'| over the cell averages
+template <int EQ, int DIM>
+__global__ void alpha_kernel(KProblem P, const double* U, double* out, long long ncell) {
+  constexpr int NC = (EQ == EQ_EULER) ? (DIM == 1 ? 3 : 4) : 1;
+  constexpr int NM = DIM == 1 ? 2 : 3;
+  double m0 = 0.0, m1 = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    double u[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) u[c] = U[(size_t)(c * NM) * ncell + q];
+    if constexpr (EQ == EQ_EULER) {
+      double s0 = euler_speed<DIM>(P, 0, u);
+      double s1 = DIM == 2 ? euler_speed<DIM>(P, 1, u) : 0.0;
+      if (!(s0 >= 0.0)) s0 = __longlong_as_double(0x7ff0000000000000ULL);
+      if (!(s1 >= 0.0)) s1 = __longlong_as_double(0x7ff0000000000000ULL);
+      m0 = fmax(m0, s0);
+      m1 = fmax(m1, s1);
+    } else {
+      m0 = fmax(m0, Phys<EQ, double>::speed(P, 0, u));
+      if (DIM == 2) m1 = fmax(m1, Phys<EQ, double>::speed(P, 1, u));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+    m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+  }
+  __shared__ double r0[32], r1[32];
+  if ((threadIdx.x & 31) == 0) {
+    r0[threadIdx.x >> 5] = m0;
+    r1[threadIdx.x >> 5] = m1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      m0 = fmax(m0, r0[w]);
+      m1 = fmax(m1, r1[w]);
+    }
+    m0 = fmax(m0, r0[0]);
+    m1 = fmax(m1, r1[0]);
+    atomic_max_nonneg(&out[0], m0);
+    atomic_max_nonneg(&out[1], m1);
+  }
+}
+
+cudaError_t launch_alpha(int eq, int dim, const KProblem& P, const double* U, double* out,
+                         cudaStream_t st) {
+  const long long ncell = (long long)P.nx * P.ny;
+  int blocks = (int)std::min<long long>((ncell + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  if (dim == 1) {
+    if (eq == EQ_ADV) alpha_kernel<EQ_ADV, 1><<<blocks, 256, 0, st>>>(P, U, out, ncell);
+    else if (eq == EQ_BURG) alpha_kernel<EQ_BURG, 1><<<blocks, 256, 0, st>>>(P, U, out, ncell);
+    else alpha_kernel<EQ_EULER, 1><<<blocks, 256, 0, st>>>(P, U, out, ncell);
+  } else {
+    if (eq == EQ_ADV) alpha_kernel<EQ_ADV, 2><<<blocks, 256, 0, st>>>(P, U, out, ncell);
+    else if (eq == EQ_BURG) alpha_kernel<EQ_BURG, 2><<<blocks, 256, 0, st>>>(P, U, out, ncell);
+    else alpha_kernel<EQ_EULER, 2><<<blocks, 256, 0, st>>>(P, U, out, ncell);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// host helpers
+int problem_check(const hweno_problem* p, std::string* why) {
+  auto bad = [&](const char* m) {
+    if (why) *why = m;
+    return HWENO_ERR_ARG;
+  };
+  if (!p) return bad("problem is NULL");
+  if (p->dim != 1 && p->dim != 2) return bad("dim must be 1 or 2");
+  if (p->equation < 0 || p->equation > 2) return bad("unknown equation");
+  if (p->nx < 2 || (p->dim == 2 && p->ny < 2)) return bad("need at least 2 cells per direction");
+  if (p->dim == 1 && p->ny != 1) return bad("ny must be 1 in 1D");
+  if ((long long)p->nx * p->ny > (1LL << 31)) return bad("grid too large");
+  if (!(p->x1 > p->x0) || (p->dim == 2 && !(p->y1 > p->y0))) return bad("empty domain");
+  for (int s = 0; s < (p->dim == 2 ? 4 : 2); ++s)
+    if (p->bc[s] < 0 || p->bc[s] > 2) return bad("unknown boundary condition");
+  if ((p->bc[0] == HWENO_BC_PERIODIC) != (p->bc[1] == HWENO_BC_PERIODIC))
+    return bad("periodic x boundaries must be periodic on both sides");
+  if (p->dim == 2 && (p->bc[2] == HWENO_BC_PERIODIC) != (p->bc[3] == HWENO_BC_PERIODIC))
+    return bad("periodic y boundaries must be periodic on both sides");
+  if (p->dim == 2) {
+    const double dx = (p->x1 - p->x0) / p->nx, dy = (p->y1 - p->y0) / p->ny;
+    if (std::fabs(dx - dy) > 1e-12 * std::max(dx, dy))
+      return bad("2D cells must be square (dx == dy): Eq. 2.20 assumes it");
+  }
+  if (p->precision != HWENO_FP64 && p->precision != HWENO_MIXED32) return bad("unknown precision");
+  if (p->weights != HWENO_W_SCALE_INVARIANT && p->weights != HWENO_W_ORIGINAL)
+    return bad("unknown weights");
+  const double gmax = p->dim == 1 ? 0.5 : 0.25;
+  if (!(p->gamma_lo > 0.0 && p->gamma_lo < gmax)) return bad("gamma_lo out of range");
+  if (!(p->eps > 0.0)) return bad("eps must be > 0");
+  if (!(p->cfl > 0.0) && !(p->dt_fixed > 0.0)) return bad("need cfl > 0 or dt_fixed > 0");
+  if (p->equation == HWENO_EULER && !(p->gamma > 1.0)) return bad("gamma must be > 1");
+  return HWENO_OK;
+}
+
+int ncomp_of(const hweno_problem* p) {
+  return p->equation == HWENO_EULER ? (p->dim == 1 ? 3 : 4) : 1;
+}
+int nmom_of(const hweno_problem* p) { return p->dim == 1 ? 2 : 3; }
+
+KProblem kproblem_of(const hweno_problem* p) {
+  KProblem k;
+  k.nx = p->nx;
+  k.ny = p->ny;
+  k.dx = (p->x1 - p->x0) / p->nx;
+  k.dy = p->dim == 2 ? (p->y1 - p->y0) / p->ny : 1.0;
+  k.inv_dx = 1.0 / k.dx;
+  k.inv_dy = 1.0 / k.dy;
+  for (int s = 0; s < 4; ++s) k.bc[s] = (p->dim == 2 || s < 2) ? p->bc[s] : HWENO_BC_PERIODIC;
+  k.ax = p->ax;
+  k.ay = p->ay;
+  k.gam = p->gamma;
+  k.wmode = p->weights;
+  k.glo = p->gamma_lo;
+  k.eps = p->eps;
+  return k;
+}
+
+cudaError_t launch_stage(const hweno_problem* p, const KProblem& kp, const KStage& S,
+                         cudaStream_t st) {
+  const bool ch = (p->equation == HWENO_EULER) && p->characteristic;
+  const bool mixed = p->precision == HWENO_MIXED32;
+  if (p->dim == 1) return launch_stage1d(p->equation, ch, mixed, kp, S, st);
+  return launch_stage2d(p->equation, ch, mixed, kp, S, st);
+}
+
+double now_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// ------------------------------------------------------------------------------------
+// solves
+struct Solve {
+  hweno_problem prob;
+  KProblem kp;
+  int nc = 0, nm = 0;
+  size_t ncell = 0, nU = 0, nV = 0;
+  double* U0 = nullptr;
+  double* U1 = nullptr;
+  double* U2 = nullptr;
+  double* Vh = nullptr;
+  DevScal* sc = nullptr;
+  DevScal* host = nullptr;  // pinned mirror of the scalars
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  size_t bytes = 0;
+};
+
+size_t solve_bytes(const hweno_problem* p) {
+  const size_t ncell = (size_t)p->nx * p->ny;
+  const int nc = ncomp_of(p), nm = nmom_of(p);
+  return sizeof(double) * ncell * (size_t)(3 * nc * nm + nc * (nm - 1)) + sizeof(DevScal);
+}
+
+void solve_free(Solve* s) {
+  if (!s) return;
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  cudaFree(s->U0);
+  cudaFree(s->U1);
+  cudaFree(s->U2);
+  cudaFree(s->Vh);
+  cudaFree(s->sc);
+  cudaFreeHost(s->host);
+  delete s;
+}
+
+// enqueue: one time step of a solve on a stream
+cudaError_t enqueue_step(Solve* s, cudaStream_t st) {
+  dt_kernel<<<1, 32, 0, st>>>(s->sc, s->kp.inv_dx, s->kp.inv_dy, s->prob.dim);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const double* in[3] = {s->U0, s->U1, s->U2};
+  double* out[3] = {s->U1, s->U2, s->U0};
+  for (int k = 1; k <= 3; ++k) {
+    KStage S;
+    S.Uin = in[k - 1];
+    S.Un = s->U0;
+    S.Vh = s->Vh;
+    S.Uout = out[k - 1];
+    S.alpha_in = s->sc->alpha[k - 1];
+    S.alpha_out = (k < 3) ? s->sc->alpha[k] : s->sc->alpha[3];
+    S.dt = &s->sc->dt;
+    S.status = &s->sc->status;
+    S.active = &s->sc->active;
+    S.k = k;
+    e = launch_stage(&s->prob, s->kp, S, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace hw
+
+using namespace hw;
+
+struct hweno_engine {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::recursive_mutex mu;
+  std::map<uint64_t, Solve*> solves;
+  uint64_t next_id = 1;
+  std::string err;
+  uint64_t budget = 0;
+  uint64_t used = 0;
+  int max_slots = 256;
+  Server* server = nullptr;
+};
+
+static int fail(hweno_engine* e, int code, const std::string& m) {
+  if (e) e->err = m;
+  return code;
+}
+static int cuda_fail(hweno_engine* e, cudaError_t c, const char* where) {
+  if (e) e->err = std::string(where) + ": " + cudaGetErrorString(c);
+  return c == cudaErrorMemoryAllocation ? HWENO_ERR_OOM : HWENO_ERR_CUDA;
+}
+#define CUDA_TRY(eng, call)                                   \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return cuda_fail(eng, _e, #call);  \
+  } while (0)
+
+extern "C" {
+
+int hweno_ncomp(const hweno_problem* p) {
+  return problem_check(p, nullptr) == HWENO_OK ? ncomp_of(p) : 0;
+}
+int hweno_nmom(const hweno_problem* p) {
+  return problem_check(p, nullptr) == HWENO_OK ? nmom_of(p) : 0;
+}
+
+int hweno_create(const hweno_engine_config* cfg, hweno_engine** out) {
+  if (!out) return HWENO_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HWENO_ERR_CUDA;
+  const int dev = cfg ? cfg->device : 0;
+  if (dev < 0 || dev >= ndev) return HWENO_ERR_ARG;
+  if (cudaSetDevice(dev) != cudaSuccess) return HWENO_ERR_CUDA;
+  hweno_engine* e = new hweno_engine();
+  e->device = dev;
+  if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete e;
+    return HWENO_ERR_CUDA;
+  }
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  e->budget = (cfg && cfg->hbm_budget_bytes) ? cfg->hbm_budget_bytes : (uint64_t)(0.9 * fr);
+  e->max_slots = (cfg && cfg->max_slots > 0) ? cfg->max_slots : 256;
+  e->server = server_create(e, cfg ? cfg->server_thread : 0);
+  *out = e;
+  return HWENO_OK;
+}
+
+void hweno_destroy(hweno_engine* e) {
+  if (!e) return;
+  server_destroy(e->server);
+  {
+    std::lock_guard<std::recursive_mutex> lk(e->mu);
+    cudaSetDevice(e->device);
+    cudaStreamSynchronize(e->stream);
+    for (auto& kv : e->solves) solve_free(kv.second);
+    e->solves.clear();
+    cudaStreamDestroy(e->stream);
+  }
+  delete e;
+}
+
+const char* hweno_last_error(const hweno_engine* e) { return e ? e->err.c_str() : "no engine"; }
+
+void* hweno_engine_stream(hweno_engine* e) { return e ? (void*)e->stream : nullptr; }
+
+}  // extern "C"
+
+// ---- internal entry points shared with the server ------------------------------------
+namespace hw {
+
+int engine_alloc_solve(hweno_engine* e, const hweno_problem* p, Solve** out) {
+  std::string why;
+  int rc = problem_check(p, &why);
+  if (rc != HWENO_OK) return fail(e, rc, why);
+  const size_t bytes = solve_bytes(p);
+  if (e->used + bytes > e->budget) return fail(e, HWENO_ERR_BUSY, "over the memory budget");
+  Solve* s = new Solve();
+  s->prob = *p;
+  s->kp = kproblem_of(p);
+  s->nc = ncomp_of(p);
+  s->nm = nmom_of(p);
+  s->ncell = (size_t)p->nx * p->ny;
+  s->nU = s->ncell * s->nc * s->nm;
+  s->nV = s->ncell * s->nc * (s->nm - 1);
+  s->bytes = bytes;
+  cudaError_t c = cudaSuccess;
+  if (c == cudaSuccess) c = cudaMalloc(&s->U0, sizeof(double) * s->nU);
+  if (c == cudaSuccess) c = cudaMalloc(&s->U1, sizeof(double) * s->nU);
+  if (c == cudaSuccess) c = cudaMalloc(&s->U2, sizeof(double) * s->nU);
+  if (c == cudaSuccess) c = cudaMalloc(&s->Vh, sizeof(double) * s->nV);
+  if (c == cudaSuccess) c = cudaMalloc(&s->sc, sizeof(DevScal));
+  if (c == cudaSuccess) c = cudaMallocHost(&s->host, sizeof(DevScal));
+  if (c != cudaSuccess) {
+    solve_free(s);
+    cudaGetLastError();
+    return cuda_fail(e, c, "allocating a solve");
+  }
+  e->used += bytes;
+  *out = s;
+  return HWENO_OK;
+}
+
+void engine_release_solve(hweno_engine* e, Solve* s) {
+  if (!s) return;
+  e->used -= std::min<uint64_t>(e->used, s->bytes);
+  solve_free(s);
+}
+
+// upload moments and time; set the scalars; compute the speeds of the state
+int engine_load_state(hweno_engine* e, Solve* s, const double* host, double t, cudaStream_t st) {
+  if (host) CUDA_TRY(e, cudaMemcpyAsync(s->U0, host, sizeof(double) * s->nU,
+                                        cudaMemcpyHostToDevice, st));
+  DevScal* h = s->host;
+  CUDA_TRY(e, cudaStreamSynchronize(st));
+  std::memset(h, 0, sizeof(DevScal));
+  h->t = t;
+  h->t_end = t;
+  h->dt_fixed = s->prob.dt_fixed;
+  h->cfl = s->prob.cfl;
+  h->steps = 0;
+  h->step_limit = 0;
+  CUDA_TRY(e, cudaMemcpyAsync(s->sc, h, sizeof(DevScal), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(e, launch_alpha(s->prob.equation, s->prob.dim, s->kp, s->U0, s->sc->alpha[3], st));
+  CUDA_TRY(e, cudaStreamSynchronize(st));
+  return HWENO_OK;
+}
+
+// set the run target on the device (t_end, absolute step limit)
+int engine_set_target(hweno_engine* e, Solve* s, double t_end, long long step_limit,
+                      cudaStream_t st) {
+  CUDA_TRY(e, cudaMemcpyAsync(s->host, s->sc, sizeof(DevScal), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(e, cudaStreamSynchronize(st));
+  s->host->t_end = t_end;
+  s->host->step_limit = step_limit;
+  CUDA_TRY(e, cudaMemcpyAsync(&s->sc->t_end, &s->host->t_end, sizeof(double),
+                              cudaMemcpyHostToDevice, st));
+  CUDA_TRY(e, cudaMemcpyAsync(&s->sc->step_limit, &s->host->step_limit, sizeof(long long),
+                              cudaMemcpyHostToDevice, st));
+  return HWENO_OK;
+}
+
+int engine_read_scalars(hweno_engine* e, Solve* s, cudaStream_t st) {
+  CUDA_TRY(e, cudaMemcpyAsync(s->host, s->sc, sizeof(DevScal), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(e, cudaStreamSynchronize(st));
+  return HWENO_OK;
+}
+
+static int ensure_graph(hweno_engine* e, Solve* s, int steps) {
+  if (s->graph && s->graph_steps == steps) return HWENO_OK;
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  cudaGraph_t g;
+  CUDA_TRY(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t c = cudaSuccess;
+  for (int k = 0; k < steps && c == cudaSuccess; ++k) c = enqueue_step(s, e->stream);
+  cudaError_t c2 = cudaStreamEndCapture(e->stream, &g);
+  if (c != cudaSuccess) return cuda_fail(e, c, "capturing the step graph");
+  if (c2 != cudaSuccess) return cuda_fail(e, c2, "ending the capture");
+  c = cudaGraphInstantiate(&s->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (c != cudaSuccess) return cuda_fail(e, c, "instantiating the step graph");
+  s->graph_steps = steps;
+  return HWENO_OK;
+}
+
+// run until t_end or the step limit; graph replays in batches, scalars read between batches
+int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps,
+               long long* steps_taken) {
+  int rc = engine_read_scalars(e, s, e->stream);
+  if (rc) return rc;
+  const long long steps0 = s->host->steps;
+  const long long limit = max_steps < 0 ? (1LL << 62) : steps0 + max_steps;
+  rc = engine_set_target(e, s, t_end, limit, e->stream);
+  if (rc) return rc;
+  const int G = 4;  // steps per graph
+  rc = ensure_graph(e, s, G);
+  if (rc) return rc;
+  long long batch = 1;
+  for (;;) {
+    for (long long b = 0; b < batch; ++b) CUDA_TRY(e, cudaGraphLaunch(s->graph, e->stream));
+    rc = engine_read_scalars(e, s, e->stream);
+    if (rc) return rc;
+    if (s->host->status) break;
+    if (!(s->host->t < t_end) || s->host->steps >= limit) break;
+    // size the next batch from the steps left at the current dt
+    double left = (t_end - s->host->t) / std::max(s->host->dt, 1e-300);
+    long long want = (long long)std::min<double>(left, (double)(limit - s->host->steps));
+    batch = std::max<long long>(1, std::min<long long>(64, (want + G - 1) / G));
+  }
+  if (steps_taken) *steps_taken = s->host->steps - steps0;
+  if (s->host->status) return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
+  return HWENO_OK;
+}
+
+double solve_time(Solve* s) { return s->host->t; }
+int solve_copy_out(hweno_engine* e, Solve* s, double* host) {
+  CUDA_TRY(e, cudaMemcpyAsync(host, s->U0, sizeof(double) * s->nU, cudaMemcpyDeviceToHost,
+                              e->stream));
+  CUDA_TRY(e, cudaStreamSynchronize(e->stream));
+  return HWENO_OK;
+}
+
+Solve* engine_find(hweno_engine* e, uint64_t id) {
+  auto it = e->solves.find(id);
+  return it == e->solves.end() ? nullptr : it->second;
+}
+
+std::recursive_mutex& engine_mutex(hweno_engine* e) { return e->mu; }
+cudaStream_t engine_stream(hweno_engine* e) { return e->stream; }
+int engine_device(hweno_engine* e) { return e->device; }
+int engine_max_slots(hweno_engine* e) { return e->max_slots; }
+uint64_t engine_budget_left(hweno_engine* e) { return e->budget - std::min(e->budget, e->used); }
+void engine_set_error(hweno_engine* e, const std::string& m) { e->err = m; }
+Server* engine_server(hweno_engine* e) { return e->server; }
+
+}  // namespace hw
+
+extern "C" {
+
+int hweno_open(hweno_engine* e, const hweno_problem* p, const double* host, uint64_t* id) {
+  if (!e || !p || !host || !id) return fail(e, HWENO_ERR_ARG, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = nullptr;
+  int rc = engine_alloc_solve(e, p, &s);
+  if (rc) return rc;
+  rc = engine_load_state(e, s, host, 0.0, e->stream);
+  if (rc) {
+    engine_release_solve(e, s);
+    return rc;
+  }
+  *id = e->next_id++;
+  e->solves[*id] = s;
+  return HWENO_OK;
+}
+
+int hweno_set_state(hweno_engine* e, uint64_t id, const double* host, double t) {
+  if (!e || !host) return fail(e, HWENO_ERR_ARG, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = engine_find(e, id);
+  if (!s) return fail(e, HWENO_ERR_ARG, "unknown solve id");
+  return engine_load_state(e, s, host, t, e->stream);
+}
+
+int hweno_get_state(hweno_engine* e, uint64_t id, double* host, double* t) {
+  if (!e) return HWENO_ERR_ARG;
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = engine_find(e, id);
+  if (!s) return fail(e, HWENO_ERR_ARG, "unknown solve id");
+  if (host)
+    CUDA_TRY(e, cudaMemcpyAsync(host, s->U0, sizeof(double) * s->nU, cudaMemcpyDeviceToHost,
+                                e->stream));
+  int rc = engine_read_scalars(e, s, e->stream);
+  if (rc) return rc;
+  if (t) *t = s->host->t;
+  return HWENO_OK;
+}
+
+int hweno_step(hweno_engine* e, uint64_t id, double* dt_taken) {
+  if (!e) return HWENO_ERR_ARG;
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = engine_find(e, id);
+  if (!s) return fail(e, HWENO_ERR_ARG, "unknown solve id");
+  int rc = engine_read_scalars(e, s, e->stream);
+  if (rc) return rc;
+  rc = engine_set_target(e, s, INFINITY, s->host->steps + 1, e->stream);
+  if (rc) return rc;
+  CUDA_TRY(e, enqueue_step(s, e->stream));
+  rc = engine_read_scalars(e, s, e->stream);
+  if (rc) return rc;
+  if (dt_taken) *dt_taken = s->host->dt;
+  if (s->host->status) return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
+  return HWENO_OK;
+}
+
+int hweno_advance(hweno_engine* e, uint64_t id, double t_end, int64_t max_steps,
+                  int64_t* steps_taken) {
+  if (!e) return HWENO_ERR_ARG;
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = engine_find(e, id);
+  if (!s) return fail(e, HWENO_ERR_ARG, "unknown solve id");
+  long long st = 0;
+  int rc = engine_run(e, s, t_end, max_steps, &st);
+  if (steps_taken) *steps_taken = st;
+  return rc;
+}
+
+int hweno_close(hweno_engine* e, uint64_t id) {
+  if (!e) return HWENO_ERR_ARG;
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = engine_find(e, id);
+  if (!s) return fail(e, HWENO_ERR_ARG, "unknown solve id");
+  cudaStreamSynchronize(e->stream);
+  e->solves.erase(id);
+  engine_release_solve(e, s);
+  return HWENO_OK;
+}
+
+int hweno_stage_device(const hweno_problem* p, int k, const double* U_in, const double* U_n,
+                       double* Vh, double* U_out, const double* alpha_in, double* alpha_out,
+                       const double* dt, uint32_t* status, void* stream) {
+  if (problem_check(p, nullptr) != HWENO_OK) return HWENO_ERR_ARG;
+  if (k < 1 || k > 3 || !U_in || !U_n || !Vh || !U_out || !alpha_in || !alpha_out || !dt ||
+      !status || U_out == U_in)
+    return HWENO_ERR_ARG;
+  KStage S;
+  S.Uin = U_in;
+  S.Un = U_n;
+  S.Vh = Vh;
+  S.Uout = U_out;
+  S.alpha_in = alpha_in;
+  S.alpha_out = alpha_out;
+  S.dt = dt;
+  S.status = status;
+  S.active = nullptr;
+  S.k = k;
+  cudaError_t c = launch_stage(p, kproblem_of(p), S, (cudaStream_t)stream);
+  return c == cudaSuccess ? HWENO_OK : HWENO_ERR_CUDA;
+}
+
+int hweno_alpha_device(const hweno_problem* p, const double* U, double* alpha_out, void* stream) {
+  if (problem_check(p, nullptr) != HWENO_OK || !U || !alpha_out) return HWENO_ERR_ARG;
+  cudaError_t c = launch_alpha(p->equation, p->dim, kproblem_of(p), U, alpha_out,
+                               (cudaStream_t)stream);
+  return c == cudaSuccess ? HWENO_OK : HWENO_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,535 @@
+// hweno_device.cuh -- device building blocks of the HWENO-U stage kernels (sm_103a).
+//
+// Real type R is the type of the bulk arithmetic (double on the FP64 path, float on the
+// mixed path).  Smoothness indicators, tau, u_ave and the nonlinear weights are always
+// evaluated in double (Eq. 2.9-2.11, 2.20-2.22).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hw {
+
+enum { EQ_ADV = 0, EQ_BURG = 1, EQ_EULER = 2 };
+enum { BC_PER = 0, BC_TRANS = 1, BC_REFL = 2 };
+
+// Kernel-side description of a problem (filled on the host from hweno_problem).
+struct KProblem {
+  int nx, ny;
+  double dx, dy, inv_dx, inv_dy;
+  int bc[4];
+  double ax, ay, gam;
+  int wmode;          // 0 scale-invariant, 1 original (u_ave = 1)
+  double glo, eps;    // linear weight of the low-degree polynomials, epsilon
+};
+
+// Pointers and scalars of one stage launch.
+struct KStage {
+  const double* Uin;   // stage input (stencil reads)
+  const double* Un;    // U^n (pointwise reads)
+  double* Vh;          // v-hat^n (, w-hat^n): written at k = 1, read at k = 2, 3
+  double* Uout;        // stage output (may alias Un)
+  const double* alpha_in;  // [2]
+  double* alpha_out;       // [2] atomic max
+  const double* dt;        // [1]
+  uint32_t* status;        // [1] atomic or
+  const int* active;       // [1] or null: the stage is skipped when *active == 0
+  int k;                   // stage 1, 2, 3
+};
+
+// ---------------------------------------------------------------------------------------
+// boundary conditions: map a ghost index to a stored index; returns the reflection flag
+__device__ __forceinline__ int bc_map(int i, int n, int bc_lo, int bc_hi, int& flip) {
+  flip = 0;
+  // at most two passes for |overshoot| <= 2 and n >= 2 (n >= 1 for periodic)
+#pragma unroll 1
+  for (int it = 0; it < 4 && (i < 0 || i >= n); ++it) {
+    int bc = (i < 0) ? bc_lo : bc_hi;
+    if (bc == BC_PER) {
+      i = (i < 0) ? i + n : i - n;
+    } else if (bc == BC_TRANS) {
+      i = (i < 0) ? 0 : n - 1;
+    } else {
+      i = (i < 0) ? -1 - i : 2 * n - 1 - i;
+      flip ^= 1;
+    }
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// sign of component c, moment m under an x (fx) and/or y (fy) mirror
+template <int EQ, int DIM>
+__device__ __forceinline__ double mirror_sign(int c, int m, int fx, int fy) {
+  double s = 1.0;
+  if (fx) {
+    bool neg = (m == 1);
+    if (EQ == EQ_EULER && c == 1) neg = !neg;
+    if (neg) s = -s;
+  }
+  if (DIM == 2 && fy) {
+    bool neg = (m == 2);
+    if (EQ == EQ_EULER && c == 2) neg = !neg;
+    if (neg) s = -s;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// nonlinear weights (Eq. 2.10-2.11 / 2.21-2.22), double precision
+template <int NS>
+__device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], double uave,
+                                                  const KProblem& P, double (&om)[NS]) {
+  double s = 0.0;
+#pragma unroll
+  for (int m = 1; m < NS; ++m) s += fabs(beta[0] - beta[m]);
+  s *= 1.0 / (double)(NS - 1);
+  const double tau = s * s;
+  const double ua = (P.wmode == 1) ? 1.0 : uave;
+  const double g0 = 1.0 - (double)(NS - 1) * P.glo;
+  double wt[NS];
+  double sum = 0.0;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    const double gm = (m == 0) ? g0 : P.glo;
+    const double d = fma(beta[m], ua, P.eps);
+    wt[m] = fma(gm, tau / d, gm);
+    sum += wt[m];
+  }
+  const double inv = 1.0 / sum;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) om[m] = wt[m] * inv;
+}
+
+// ---------------------------------------------------------------------------------------
+// 1D reconstruction of one field (Sec. 2.1 Steps 1-3, Eq. 2.12).
+// Inputs: averages um, u0, up of I_{i-1}, I_i, I_{i+1}; first moments vm, vp of I_{i-1},
+// I_{i+1}.  Outputs: values at the Gauss-Lobatto nodes -1/2, -sqrt5/10, sqrt5/10, 1/2
+// and v-hat.
+template <typename R>
+__device__ __forceinline__ void recon1d(R um, R u0, R up, R vm, R vp, const KProblem& P,
+                                        R (&pts)[4], R& vhat) {
+  // Step 1: Appendix, monomials of xi = (x - x_i)/dx
+  const R su = um + up, du = up - um, sv = vm + vp, dv = vp - vm;
+  const R c0 = R(-43.0 / 384.0) * su + R(235.0 / 192.0) * u0 + R(27.0 / 64.0) * dv;
+  const R c1 = R(63.0 / 76.0) * du - R(75.0 / 19.0) * sv;
+  const R c2 = R(23.0 / 16.0) * su - R(23.0 / 8.0) * u0 - R(45.0 / 8.0) * dv;
+  const R c3 = R(-5.0 / 19.0) * du + R(60.0 / 19.0) * sv;
+  const R c4 = R(-5.0 / 8.0) * su + R(5.0 / 4.0) * u0 + R(15.0 / 4.0) * dv;
+  const R l1 = u0 - um, l2 = up - u0;
+  // Step 2: Eq. 2.9 (first term with c_{0,3}, from the definition Eq. 2.8)
+  double beta[3];
+  {
+    const double d1 = c1, d2 = c2, d3 = c3, d4 = c4;
+    const double t1 = fma(0.25, d3, d1);
+    const double t2 = fma(63.0 / 130.0, d4, d2);
+    double b = t1 * t1;
+    b = fma(13.0 / 3.0 * t2, t2, b);
+    b = fma(781.0 / 20.0 * d3, d3, b);
+    b = fma(1421461.0 / 2275.0 * d4, d4, b);
+    beta[0] = b;
+    const double e1 = l1, e2 = l2;
+    beta[1] = e1 * e1;
+    beta[2] = e2 * e2;
+  }
+  // Step 3
+  const double a = ((double)fabs(um) + (double)fabs(u0) + (double)fabs(up)) * (1.0 / 3.0);
+  double om[3];
+  nonlinear_weights<3>(beta, a * a, P, om);
+  // combined polynomial u_i = a0 p_0 + sum_m (omega_m - a0 gamma_m) p_m, a0 = omega_0/gamma_0
+  const double g0 = 1.0 - 2.0 * P.glo;
+  const double a0d = om[0] / g0;
+  const R a0 = (R)a0d;
+  const R b1 = (R)(om[1] - a0d * P.glo), b2 = (R)(om[2] - a0d * P.glo);
+  const R C0 = a0 * c0 + (R)(1.0 - a0d) * u0;
+  const R C1 = a0 * c1 + b1 * l1 + b2 * l2;
+  const R C2 = a0 * c2, C3 = a0 * c3, C4 = a0 * c4;
+  // values at +-1/2 and +-sqrt(5)/10 (even / odd parts)
+  {
+    const R x = R(0.5), x2 = R(0.25), x4 = R(0.0625);
+    const R E = C0 + C2 * x2 + C4 * x4, O = x * (C1 + C3 * x2);
+    pts[0] = E - O;
+    pts[3] = E + O;
+  }
+  {
+    const R x = R(0.22360679774997896964), x2 = R(0.05), x4 = R(0.0025);
+    const R E = C0 + C2 * x2 + C4 * x4, O = x * (C1 + C3 * x2);
+    pts[1] = E - O;
+    pts[2] = E + O;
+  }
+  vhat = C1 * R(1.0 / 12.0) + C3 * R(1.0 / 80.0);
+}
+
+// ---------------------------------------------------------------------------------------
+// 2D reconstruction of one field (Sec. 2.2 Steps 1-3, Eq. 2.23).
+// u[0..8]: averages of cells 1..9 (row-major from the bottom-left, u[4] = own cell);
+// v[0..3], w[0..3]: x / y first moments of cells 2, 4, 6, 8.
+// Output: combined monomial coefficients C[15] (basis 1, xi, eta, xi^2, xi eta, eta^2,
+// xi^3, xi^2 eta, xi eta^2, eta^3, xi^4, xi^3 eta, xi^2 eta^2, xi eta^3, eta^4).
+template <typename R>
+__device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
+                                               const KProblem& P, R (&C)[15]) {
+  const R u1 = u[0], u2 = u[1], u3 = u[2], u4 = u[3], u5 = u[4], u6 = u[5], u7 = u[6],
+          u8 = u[7], u9 = u[8];
+  const R v2 = v[0], v4 = v[1], v6 = v[2], v8 = v[3];
+  const R w2 = w[0], w4 = w[1], w6 = w[2], w8 = w[3];
+  // Step 1: Appendix (c_{0,4} with -7/22 u_1), written on symmetric combinations
+  const R A = u1 + u3, B = u7 + u9, Sc = A + B;
+  const R Db = u1 - u3, Dt = u7 - u9;
+  const R X1 = Db + Dt, X2 = A - B, X3 = Db - Dt;
+  const R h = u4 + u6, e = u4 - u6, vv = u2 + u8, ve = u2 - u8;
+  const R Se = h + vv;
+  const R Va = v4 + v6, Vd = v6 - v4, Wa = w2 + w8, Wd = w8 - w2;
+  const R v82 = v8 - v2, w64 = w6 - w4;
+  R c[15];
+  c[0] = R(1.0 / 576.0) * Sc - R(133.0 / 1152.0) * Se + R(419.0 / 288.0) * u5 +
+         R(27.0 / 64.0) * (Vd + Wd);
+  c[1] = R(1.0 / 48.0) * X1 - R(397.0 / 456.0) * e - R(75.0 / 19.0) * Va;
+  c[2] = R(1.0 / 48.0) * X2 - R(397.0 / 456.0) * ve - R(75.0 / 19.0) * Wa;
+  c[3] = R(-1.0 / 48.0) * Sc + R(1.0 / 24.0) * vv + R(71.0 / 48.0) * h - R(71.0 / 24.0) * u5 -
+         R(45.0 / 8.0) * Vd;
+  c[4] = R(-7.0 / 22.0) * X3 + R(75.0 / 11.0) * (v82 + w64);
+  c[5] = R(-1.0 / 48.0) * Sc + R(71.0 / 48.0) * vv + R(1.0 / 24.0) * h - R(71.0 / 24.0) * u5 -
+         R(45.0 / 8.0) * Wd;
+  c[6] = R(5.0 / 19.0) * e + R(60.0 / 19.0) * Va;
+  c[7] = R(-0.25) * X2 + R(0.5) * ve;
+  c[8] = R(-0.25) * X1 + R(0.5) * e;
+  c[9] = R(5.0 / 19.0) * ve + R(60.0 / 19.0) * Wa;
+  c[10] = R(-5.0 / 8.0) * h + R(5.0 / 4.0) * u5 + R(15.0 / 4.0) * Vd;
+  c[11] = R(5.0 / 22.0) * X3 - R(60.0 / 11.0) * v82;
+  c[12] = R(0.25) * Sc - R(0.5) * Se + u5;
+  c[13] = R(5.0 / 22.0) * X3 - R(60.0 / 11.0) * w64;
+  c[14] = R(-5.0 / 8.0) * vv + R(5.0 / 4.0) * u5 + R(15.0 / 4.0) * Wd;
+  // linear polynomials on S_1 = {2,4,5}, S_2 = {2,5,6}, S_3 = {4,5,8}, S_4 = {5,6,8}
+  const R dl = u5 - u4, dr = u6 - u5, db = u5 - u2, dtp = u8 - u5;
+  // Step 2: Eq. 2.20 (double)
+  double beta[5];
+  {
+    double d[15];
+#pragma unroll
+    for (int n = 0; n < 15; ++n) d[n] = (double)c[n];
+    double s, t;
+    t = fma(0.5, d[6], d[1]);
+    s = t * t;
+    t = fma(1.0 / 6.0, d[8], d[1]);
+    s = fma(t, t, s);
+    t = fma(1.0 / 6.0, d[7], d[2]);
+    s = fma(t, t, s);
+    t = fma(0.5, d[9], d[2]);
+    s = fma(t, t, s);
+    double b = 0.5 * s;
+    t = fma(63.0 / 65.0, d[10], d[3]);
+    s = t * t;
+    t = fma(1.0 / 6.0, d[12], d[3]);
+    s = fma(t, t, s);
+    t = fma(1.0 / 6.0, d[12], d[5]);
+    s = fma(t, t, s);
+    t = fma(63.0 / 65.0, d[14], d[5]);
+    s = fma(t, t, s);
+    b = fma(13.0 / 6.0, s, b);
+    t = fma(17.0 / 35.0, d[11], d[4]);
+    s = t * t;
+    t = fma(17.0 / 35.0, d[13], d[4]);
+    s = fma(t, t, s);
+    b = fma(7.0 / 12.0, s, b);
+    t = fma(5.0 / 9357.0, d[8], d[6]);
+    b = fma(3119.0 / 80.0 * t, t, b);
+    t = fma(15.0 / 3379.0, d[9], d[7]);
+    b = fma(3379.0 / 720.0 * t, t, b);
+    b = fma(2634769.0 / 561420.0 * d[8], d[8], b);
+    b = fma(2634769.0 / 67580.0 * d[9], d[9], b);
+    t = fma(3185.0 / 11353166.0, d[12], d[10]);
+    b = fma(5676583.0 / 9100.0 * t, t, b);
+    t = fma(1155.0 / 709573.0, d[13], d[11]);
+    b = fma(709573.0 / 16800.0 * t, t, b);
+    t = fma(2145748374.0 / 230094013357.0, d[14], d[12]);
+    b = fma(230094013357.0 / 12261419280.0 * t, t, b);
+    b = fma(31468281769.0 / 745051650.0 * d[13], d[13], b);
+    b = fma(25118160529227568.0 / 40266452337475.0 * d[14], d[14], b);
+    beta[0] = b;
+    const double el = dl, er = dr, eb = db, et = dtp;
+    const double el2 = el * el, er2 = er * er, eb2 = eb * eb, et2 = et * et;
+    beta[1] = el2 + eb2;
+    beta[2] = er2 + eb2;
+    beta[3] = el2 + et2;
+    beta[4] = er2 + et2;
+  }
+  // Step 3
+  const double a = ((double)fabs(u2) + (double)fabs(u4) + (double)fabs(u5) + (double)fabs(u6) +
+                    (double)fabs(u8)) * 0.2;
+  double om[5];
+  nonlinear_weights<5>(beta, a * a, P, om);
+  const double g0 = 1.0 - 4.0 * P.glo;
+  const double a0d = om[0] / g0;
+  const R a0 = (R)a0d;
+  const R b1 = (R)(om[1] - a0d * P.glo), b2 = (R)(om[2] - a0d * P.glo),
+          b3 = (R)(om[3] - a0d * P.glo), b4 = (R)(om[4] - a0d * P.glo);
+  C[0] = a0 * c[0] + (R)(1.0 - a0d) * u5;
+  C[1] = a0 * c[1] + (b1 + b3) * dl + (b2 + b4) * dr;
+  C[2] = a0 * c[2] + (b1 + b2) * db + (b3 + b4) * dtp;
+#pragma unroll
+  for (int n = 3; n < 15; ++n) C[n] = a0 * c[n];
+}
+
+// Gauss node sqrt(15)/10 and powers
+#define HW_S15 0.38729833462074168852
+#define HW_S15_2 0.15
+#define HW_S15_4 0.0225
+
+// Values of the combined polynomial along xi = const lines: P_b(xi) (coefficients of eta^b)
+template <typename R>
+__device__ __forceinline__ void xi_line_pm(const R (&C)[15], R x, R x2, R x4, R (&Pm)[5],
+                                           R (&Pp)[5]) {
+  const R E0 = C[0] + C[3] * x2 + C[10] * x4, O0 = x * (C[1] + C[6] * x2);
+  const R E1 = C[2] + C[7] * x2, O1 = x * (C[4] + C[11] * x2);
+  const R E2 = C[5] + C[12] * x2, O2 = x * C[8];
+  const R E3 = C[9], O3 = x * C[13];
+  Pm[0] = E0 - O0; Pp[0] = E0 + O0;
+  Pm[1] = E1 - O1; Pp[1] = E1 + O1;
+  Pm[2] = E2 - O2; Pp[2] = E2 + O2;
+  Pm[3] = E3 - O3; Pp[3] = E3 + O3;
+  Pm[4] = C[14];   Pp[4] = C[14];
+}
+template <typename R>
+__device__ __forceinline__ void eta_line_pm(const R (&C)[15], R y, R y2, R y4, R (&Qm)[5],
+                                            R (&Qp)[5]) {
+  const R E0 = C[0] + C[5] * y2 + C[14] * y4, O0 = y * (C[2] + C[9] * y2);
+  const R E1 = C[1] + C[8] * y2, O1 = y * (C[4] + C[13] * y2);
+  const R E2 = C[3] + C[12] * y2, O2 = y * C[7];
+  const R E3 = C[6], O3 = y * C[11];
+  Qm[0] = E0 - O0; Qp[0] = E0 + O0;
+  Qm[1] = E1 - O1; Qp[1] = E1 + O1;
+  Qm[2] = E2 - O2; Qp[2] = E2 + O2;
+  Qm[3] = E3 - O3; Qp[3] = E3 + O3;
+  Qm[4] = C[10];   Qp[4] = C[10];
+}
+// quartic sum_b P_b t^b at t = -s, 0, +s
+template <typename R>
+__device__ __forceinline__ void quartic3(const R (&Pq)[5], R (&out)[3]) {
+  const R E = Pq[0] + Pq[2] * R(HW_S15_2) + Pq[4] * R(HW_S15_4);
+  const R O = R(HW_S15) * (Pq[1] + Pq[3] * R(HW_S15_2));
+  out[0] = E - O;
+  out[1] = Pq[0];
+  out[2] = E + O;
+}
+
+// x-pass points: left edge (-1/2, eta_g), right edge (+1/2, eta_g), interior (xi_g, eta_h)
+// at index 3g+h.  y-pass points: bottom (xi_g, -1/2), top (xi_g, +1/2), interior.
+template <typename R>
+__device__ __forceinline__ void eval_xpass(const R (&C)[15], R (&xl)[3], R (&xr)[3], R (&in)[9]) {
+  R Pm[5], Pp[5], q[3];
+  xi_line_pm(C, R(0.5), R(0.25), R(0.0625), Pm, Pp);
+  quartic3(Pm, xl);
+  quartic3(Pp, xr);
+  xi_line_pm(C, R(HW_S15), R(HW_S15_2), R(HW_S15_4), Pm, Pp);
+  quartic3(Pm, q);
+  in[0] = q[0]; in[1] = q[1]; in[2] = q[2];
+  quartic3(Pp, q);
+  in[6] = q[0]; in[7] = q[1]; in[8] = q[2];
+  const R P0[5] = {C[0], C[2], C[5], C[9], C[14]};
+  quartic3(P0, q);
+  in[3] = q[0]; in[4] = q[1]; in[5] = q[2];
+}
+template <typename R>
+__device__ __forceinline__ void eval_ypass(const R (&C)[15], R (&yb)[3], R (&yt)[3], R (&in)[9]) {
+  R Qm[5], Qp[5], q[3];
+  eta_line_pm(C, R(0.5), R(0.25), R(0.0625), Qm, Qp);
+  quartic3(Qm, yb);
+  quartic3(Qp, yt);
+  eta_line_pm(C, R(HW_S15), R(HW_S15_2), R(HW_S15_4), Qm, Qp);
+  quartic3(Qm, q);           // eta = -s : xi = -s, 0, s  -> interior index 3g + 0
+  in[0] = q[0]; in[3] = q[1]; in[6] = q[2];
+  quartic3(Qp, q);           // eta = +s
+  in[2] = q[0]; in[5] = q[1]; in[8] = q[2];
+  const R Q0[5] = {C[0], C[1], C[3], C[6], C[10]};
+  quartic3(Q0, q);           // eta = 0
+  in[1] = q[0]; in[4] = q[1]; in[7] = q[2];
+}
+// first-moment modifications: int int u xi = C1/12 + C6/80 + C8/144, same for eta
+template <typename R>
+__device__ __forceinline__ R vhat2d(const R (&C)[15]) {
+  return C[1] * R(1.0 / 12.0) + C[6] * R(1.0 / 80.0) + C[8] * R(1.0 / 144.0);
+}
+template <typename R>
+__device__ __forceinline__ R what2d(const R (&C)[15]) {
+  return C[2] * R(1.0 / 12.0) + C[9] * R(1.0 / 80.0) + C[7] * R(1.0 / 144.0);
+}
+
+// ---------------------------------------------------------------------------------------
+// physics
+template <int EQ, typename R>
+struct Phys;
+
+template <typename R>
+struct Phys<EQ_ADV, R> {
+  static constexpr int NC = 1;
+  __device__ static void flux(const KProblem& P, int dir, const R* u, R* f) {
+    f[0] = (R)(dir == 0 ? P.ax : P.ay) * u[0];
+  }
+  __device__ static double speed(const KProblem& P, int dir, const double* u) {
+    return fabs(dir == 0 ? P.ax : P.ay);
+  }
+};
+template <typename R>
+struct Phys<EQ_BURG, R> {
+  static constexpr int NC = 1;
+  __device__ static void flux(const KProblem&, int, const R* u, R* f) { f[0] = R(0.5) * u[0] * u[0]; }
+  __device__ static double speed(const KProblem&, int, const double* u) { return fabs(u[0]); }
+};
+
+// Euler flux in direction dir for DIM = 1 (3 comps) or 2 (4 comps)
+template <int DIM, typename R>
+__device__ __forceinline__ void euler_flux(const KProblem& P, int dir, const R* u, R* f) {
+  const R gm1 = (R)(P.gam - 1.0);
+  if (DIM == 1) {
+    const R vel = u[1] / u[0];
+    const R p = gm1 * (u[2] - R(0.5) * u[1] * vel);
+    f[0] = u[1];
+    f[1] = u[1] * vel + p;
+    f[2] = vel * (u[2] + p);
+  } else {
+    const R ir = R(1) / u[0];
+    const R vx = u[1] * ir, vy = u[2] * ir;
+    const R p = gm1 * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
+    if (dir == 0) {
+      f[0] = u[1];
+      f[1] = u[1] * vx + p;
+      f[2] = u[2] * vx;
+      f[3] = vx * (u[3] + p);
+    } else {
+      f[0] = u[2];
+      f[1] = u[1] * vy;
+      f[2] = u[2] * vy + p;
+      f[3] = vy * (u[3] + p);
+    }
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ double euler_speed(const KProblem& P, int dir, const double* u) {
+  const double ir = 1.0 / u[0];
+  if (DIM == 1) {
+    const double vel = u[1] * ir;
+    const double p = (P.gam - 1.0) * (u[2] - 0.5 * u[1] * vel);
+    return fabs(vel) + sqrt(P.gam * p * ir);
+  }
+  const double vx = u[1] * ir, vy = u[2] * ir;
+  const double p = (P.gam - 1.0) * (u[3] - 0.5 * (u[1] * vx + u[2] * vy));
+  return fabs(dir == 0 ? vx : vy) + sqrt(P.gam * p * ir);
+}
+
+template <int DIM>
+__device__ __forceinline__ bool euler_physical(const KProblem& P, const double* u) {
+  if (!(u[0] > 0.0)) return false;
+  double kin;
+  if (DIM == 1) kin = 0.5 * u[1] * u[1] / u[0];
+  else kin = 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0];
+  const double e = u[DIM + 1] - kin;
+  return e > 0.0 && isfinite(e);
+}
+
+// Characteristic decomposition of the Euler equations (Remark 2.2): eigenvectors of the
+// flux Jacobian at a state.  1D columns: u-c, u, u+c.  2D x: u-c, u, shear, u+c (the y
+// Jacobian exchanges the roles of the velocity components).
+template <typename R>
+struct Eig1 {
+  R u, c, ic2, H, b1h, b2h, hic;  // half-scaled constants of L
+  __device__ __forceinline__ bool init(const KProblem& P, R rho, R m, R E) {
+    const R ir = R(1) / rho;
+    u = m * ir;
+    const R gm1 = (R)(P.gam - 1.0);
+    const R p = gm1 * (E - R(0.5) * m * u);
+    const R c2 = (R)P.gam * p * ir;
+    c = sqrt(c2);
+    H = (E + p) * ir;
+    const R b1 = gm1 / c2;
+    b1h = R(0.5) * b1;
+    b2h = R(0.5) * (R(0.5) * u * u * b1);
+    hic = R(0.5) / c;
+    return p > R(0) && rho > R(0);
+  }
+  // W = L U: s = (b2 U0 - b1 (u U1 - U2))/2, t = (u U0 - U1)/(2c): W0 = s+t, W1 = U0-2s, W2 = s-t
+  __device__ __forceinline__ void project(const R* U, R* W) const {
+    const R s = b2h * U[0] - b1h * (u * U[1] - U[2]);
+    const R t = (u * U[0] - U[1]) * hic;
+    W[0] = s + t;
+    W[1] = U[0] - R(2) * s;
+    W[2] = s - t;
+  }
+  __device__ __forceinline__ R project_field(int f, const R* U) const {
+    const R s = b2h * U[0] - b1h * (u * U[1] - U[2]);
+    if (f == 1) return U[0] - R(2) * s;
+    const R t = (u * U[0] - U[1]) * hic;
+    return f == 0 ? s + t : s - t;
+  }
+  // U = R W
+  __device__ __forceinline__ void unproject(const R* W, R* U) const {
+    const R S = W[0] + W[1] + W[2];
+    const R D = W[2] - W[0];
+    U[0] = S;
+    U[1] = u * S + c * D;
+    U[2] = H * (W[0] + W[2]) + u * c * D + R(0.5) * u * u * W[1];
+  }
+};
+
+template <typename R>
+struct Eig2 {
+  R un, ut, c, H, q2h, b1h, b2h, hic;  // un: normal velocity, ut: tangential velocity
+  int dir;
+  __device__ __forceinline__ bool init(const KProblem& P, int d, const R* U) {
+    dir = d;
+    const R ir = R(1) / U[0];
+    const R vx = U[1] * ir, vy = U[2] * ir;
+    un = d == 0 ? vx : vy;
+    ut = d == 0 ? vy : vx;
+    const R gm1 = (R)(P.gam - 1.0);
+    q2h = R(0.5) * (vx * vx + vy * vy);
+    const R p = gm1 * (U[3] - U[0] * q2h);
+    const R c2 = (R)P.gam * p * ir;
+    c = sqrt(c2);
+    H = (U[3] + p) * ir;
+    const R b1 = gm1 / c2;
+    b1h = R(0.5) * b1;
+    b2h = q2h * b1h;
+    hic = R(0.5) / c;
+    return p > R(0) && U[0] > R(0);
+  }
+  // components in the rotated frame: n = normal momentum, t = tangential momentum
+  __device__ __forceinline__ R project_field(int f, const R* U) const {
+    const R mn = dir == 0 ? U[1] : U[2];
+    const R mt = dir == 0 ? U[2] : U[1];
+    if (f == 2) return mt - ut * U[0];              // shear
+    const R s = b2h * U[0] - b1h * (un * mn + ut * mt - U[3]);
+    if (f == 1) return U[0] - R(2) * s;             // entropy
+    const R t = (un * U[0] - mn) * hic;
+    return f == 0 ? s + t : s - t;                  // u-c, u+c
+  }
+  // U = R W (columns u-c, u, shear, u+c in the rotated frame)
+  __device__ __forceinline__ void unproject(const R* W, R* U) const {
+    const R S = W[0] + W[1] + W[3];
+    const R D = W[3] - W[0];
+    const R mn = un * S + c * D;
+    const R mt = ut * S + W[2];
+    U[0] = S;
+    if (dir == 0) { U[1] = mn; U[2] = mt; } else { U[1] = mt; U[2] = mn; }
+    U[3] = H * (W[0] + W[3]) + (un * c) * D + q2h * W[1] + ut * W[2];
+  }
+  // U += R[:, f] * w for field f
+  __device__ __forceinline__ void unproject_add(int f, R w, R* U) const {
+    R mn, mt, e, r0;
+    if (f == 0) { r0 = w; mn = (un - c) * w; mt = ut * w; e = (H - un * c) * w; }
+    else if (f == 1) { r0 = w; mn = un * w; mt = ut * w; e = q2h * w; }
+    else if (f == 2) { r0 = R(0); mn = R(0); mt = w; e = ut * w; }
+    else { r0 = w; mn = (un + c) * w; mt = ut * w; e = (H + un * c) * w; }
+    U[0] += r0;
+    if (dir == 0) { U[1] += mn; U[2] += mt; } else { U[1] += mt; U[2] += mn; }
+    U[3] += e;
+  }
+};
+
+// atomic max of a non-negative double (bit pattern order = value order for x >= 0)
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ULL);  // NaN -> +inf
+  atomicMax(reinterpret_cast<unsigned long long*>(addr),
+            (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace hw

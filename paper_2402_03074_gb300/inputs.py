@@ -262,7 +262,7 @@ def _vortex_perturbation(x, y, xc, yc, gam=GAMMA, beta=VORTEX_BETA, R=VORTEX_R):
     return du, dv, 1.0 + dT
 
 
-def quadrant_vortex_2d(seed: int, n: int, steps: int = 200) -> Workload:
+def _quadrant_vortex_func(seed: int):
     rng = np.random.default_rng(seed)
     rho = rng.uniform(0.1, 2.0, size=4)
     prs = rng.uniform(0.1, 2.0, size=4)
@@ -277,9 +277,26 @@ def quadrant_vortex_2d(seed: int, n: int, steps: int = 200) -> Workload:
         p = prs[q] * T ** (GAMMA / (GAMMA - 1.0))
         return euler_conserved(r, uu[q] + du, p, v=vv[q] + dv)
 
-    return Workload(f"quadrant_vortex_2d_s{seed}_n{n}", 2, EULER, n, n, 0.0, 1.0, 0.0, 1.0,
-                    (BC_TRANSMISSIVE,) * 4, float("inf"), moments_2d(f, 0.0, 1.0, 0.0, 1.0, n, n),
-                    meta=dict(rho=rho, p=prs, u=uu, v=vv, xc=(xc, yc), steps=steps))
+    return f, dict(rho=rho, p=prs, u=uu, v=vv, xc=(xc, yc))
+
+
+def quadrant_vortex_2d(seed: int, n: int, steps: int = 200, window=None) -> Workload:
+    """Seeded 4-quadrant Riemann data with an isentropic vortex on the unit square, n x n
+    cells, transmissive.  window = (i0, j0, w, h) returns only that block of cells of the
+    n x n grid (same cell size), as its own transmissive w x h problem."""
+    f, meta = _quadrant_vortex_func(seed)
+    meta["steps"] = steps
+    h = 1.0 / n
+    if window is None:
+        U0 = moments_2d(f, 0.0, 1.0, 0.0, 1.0, n, n)
+        return Workload(f"quadrant_vortex_2d_s{seed}_n{n}", 2, EULER, n, n, 0.0, 1.0, 0.0, 1.0,
+                        (BC_TRANSMISSIVE,) * 4, float("inf"), U0, meta=meta)
+    i0, j0, w, hh = window
+    x0, y0 = i0 * h, j0 * h
+    U0 = moments_2d(f, x0, x0 + w * h, y0, y0 + hh * h, w, hh)
+    return Workload(f"quadrant_vortex_2d_s{seed}_n{n}_win{i0}_{j0}_{w}x{hh}", 2, EULER, w, hh,
+                    x0, x0 + w * h, y0, y0 + hh * h, (BC_TRANSMISSIVE,) * 4, float("inf"), U0,
+                    meta=meta)
 
 
 def vortex_periodic_2d(n: int, t_end: float = 0.05) -> Workload:

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerance (FP64 path): |gpu - oracle| <= 1e-12 * max(|oracle|, S_c) per cell and moment,
+S_c = max |cell average| of component c (first moments are measured against the same scale).
+Every stage is checked from identical inputs; grids span several blocks / bands with ragged
+tails; all boundary conditions; scalar and Euler; characteristic and component-wise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2402_03074_gb300 import _binding as H
+from paper_2402_03074_gb300 import inputs as I
+
+from gpu_helpers import gpu_stage, problems, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+CASES_1D = [("adv", 0, 1), ("burg", 0, 1), ("burg", 1, 1), ("euler", 1, 1), ("euler", 1, 0),
+            ("euler", 2, 1), ("euler", 0, 1)]
+CASES_2D = [("adv", 0, 1), ("burg", 1, 1), ("euler", 1, 1), ("euler", 0, 1), ("euler", 2, 1),
+            ("euler", 1, 0), ("euler", (1, 2, 2, 1), 1)]
+
+
+def _inputs(op, seed):
+    eq = {O.ADVECTION: I.ADVECTION, O.BURGERS: I.BURGERS, O.EULER: I.EULER}[op.eq]
+    Uin = I.random_state(op.shape, seed, eq=eq)
+    Un = I.random_state(op.shape, seed + 1, eq=eq)
+    Vh = np.random.default_rng(seed + 2).uniform(-0.05, 0.05, size=(op.ncomp, op.nmom - 1, op.ny, op.nx))
+    return Uin, Un, Vh
+
+
+def _check_stage(op, hp, k, seed, tol=TOL):
+    Uin, Un, Vh = _inputs(op, seed)
+    if k == 1:
+        Un = Uin
+    alpha = O.alpha(op, Uin)
+    dt = 0.3 / (alpha[0] / ((op.x1 - op.x0) / op.nx) + (alpha[1] / ((op.y1 - op.y0) / op.ny) if op.dim == 2 else 0.0))
+    ref, vref, ost = O.stage(op, k, Uin, Un, Vh if k > 1 else None, alpha, dt)
+    got, vgot, a_out, st = gpu_stage(hp, k, Uin, Un, Vh, alpha, dt)
+    assert st == ost == 0
+    e = rel_err(got, ref, Uin)
+    assert e <= tol, f"stage {k}: max rel err {e:.3e}"
+    if k == 1:
+        ev = rel_err(vgot, vref, Uin)
+        assert ev <= tol, f"v-hat: {ev:.3e}"
+    aref = O.alpha(op, ref)
+    np.testing.assert_allclose(a_out[: op.dim], aref[: op.dim], rtol=1e-13)
+    return e
+
+
+@pytest.mark.parametrize("eq,bc,ch", CASES_1D)
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_stage_1d(eq, bc, ch, k):
+    op, hp = problems(1, eq, 301, bc=bc, characteristic=ch)   # 3 blocks, ragged tail
+    _check_stage(op, hp, k, seed=10 * k)
+
+
+@pytest.mark.parametrize("eq,bc,ch", CASES_2D)
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_stage_2d(eq, bc, ch, k):
+    op, hp = problems(2, eq, 261, 23, bc=bc, characteristic=ch)  # 3 bands, ragged tail
+    _check_stage(op, hp, k, seed=20 * k)
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (126, 3), (127, 4), (128, 9), (252, 2)])
+def test_stage_2d_edge_sizes(nx, ny):
+    """Grids of 2 cells, band-width multiples and +-1, single-row chunks."""
+    op, hp = problems(2, "euler", nx, ny, bc=1)
+    _check_stage(op, hp, 1, seed=5)
+    _check_stage(op, hp, 2, seed=6)
+
+
+@pytest.mark.parametrize("n", [2, 3, 125, 126, 127, 253])
+def test_stage_1d_edge_sizes(n):
+    op, hp = problems(1, "euler", n, bc=1)
+    _check_stage(op, hp, 3, seed=7)
+
+
+def test_weights_original_variant():
+    op, hp = problems(2, "euler", 40, 30, bc=1, weights=1)
+    _check_stage(op, hp, 1, seed=8)
+    op, hp = problems(1, "burg", 90, bc=0, weights=1)
+    _check_stage(op, hp, 2, seed=9)
+
+
+def _oracle_of(hp):
+    eq = {H.HWENO_ADVECTION: O.ADVECTION, H.HWENO_BURGERS: O.BURGERS, H.HWENO_EULER: O.EULER}[hp.equation]
+    return O.Problem(dim=hp.dim, eq=eq, nx=hp.nx, ny=hp.ny, x0=hp.x0, x1=hp.x1, y0=hp.y0, y1=hp.y1,
+                     ax=hp.ax, ay=hp.ay, gam=hp.gamma, bc=tuple(hp.bc), characteristic=hp.characteristic,
+                     weights=hp.weights, gamma_lo=hp.gamma_lo, eps=hp.eps, cfl=hp.cfl)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_engine_steps_match_oracle(dim):
+    """hweno_open + hweno_step x3 + hweno_get_state vs the oracle's steps (CFL rule)."""
+    if dim == 1:
+        w = I.shock_tube_1d(3, n=400)
+        hp = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
+    else:
+        w = I.quadrant_vortex_2d(1, 64)
+        hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1,
+                            y0=w.y0, y1=w.y1, bc=w.bc)
+    op = _oracle_of(hp)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, w.U0)
+        U = w.U0.copy()
+        t = 0.0
+        for s in range(3):
+            dt_gpu = H.hweno_step(eng, sid)
+            U, t, dt_o, st = O.step(op, U, t)
+            assert st == 0
+            assert dt_gpu == pytest.approx(dt_o, rel=1e-13)
+            got, tg = H.hweno_get_state(eng, sid, np.empty_like(U))
+            assert tg == pytest.approx(t, rel=1e-14)
+            e = rel_err(got, U, w.U0)
+            assert e <= 1e-12 * (s + 1), f"step {s}: {e:.3e}"
+        H.hweno_close(eng, sid)
+    finally:
+        H.hweno_destroy(eng)
+
+
+def test_advance_lands_on_t_end_and_matches_oracle():
+    """Config-1 run: u_t + u_x = 0, N = 200, CFL 0.6, T = 2 (334 steps, last one clipped)."""
+    w = I.advection_sine_1d(200)
+    hp = H.make_problem(dim=1, equation=H.HWENO_ADVECTION, nx=200, x0=0.0, x1=2.0, ax=1.0)
+    op = _oracle_of(hp)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, w.U0)
+        n = H.hweno_advance(eng, sid, 2.0)
+        got, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+    finally:
+        H.hweno_destroy(eng)
+    U, to, ns, st = O.run(op, w.U0, 0.0, 2.0)
+    assert n == ns == 334 and t == 2.0 and to == 2.0
+    assert rel_err(got, U, w.U0) <= 1e-11
+    ex = I.advection_exact_1d(200, 2.0)
+    assert np.abs(got[0, 0] - ex[0, 0]).max() == pytest.approx(1.7704e-6, rel=0.01)
+
+
+def test_advance_max_steps_and_checkpoint_restore():
+    w = I.quadrant_vortex_2d(2, 48)
+    hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=48, ny=48, x0=0, x1=1, y0=0, y1=1, bc=w.bc)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, w.U0)
+        assert H.hweno_advance(eng, sid, 10.0, max_steps=5) == 5
+        mid, tm = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        assert H.hweno_advance(eng, sid, 10.0, max_steps=3) == 3
+        a, ta = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        H.hweno_set_state(eng, sid, mid, tm)           # restore the checkpoint
+        assert H.hweno_advance(eng, sid, 10.0, max_steps=3) == 3
+        b, tb = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        np.testing.assert_array_equal(a, b)            # bit-reproducible
+        assert ta == tb
+    finally:
+        H.hweno_destroy(eng)
+
+
+def test_conservation_periodic_gpu():
+    w = I.euler_density_wave_2d(64, t_end=0.05)
+    hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=64, ny=64, x0=0, x1=4, y0=0, y1=4)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, w.U0)
+        H.hweno_advance(eng, sid, 0.05)
+        got, _ = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+    finally:
+        H.hweno_destroy(eng)
+    s0 = w.U0[:, 0].sum(axis=(1, 2))
+    s1 = got[:, 0].sum(axis=(1, 2))
+    assert (np.abs(s1 - s0) <= 1e-14 * np.abs(w.U0[:, 0]).sum(axis=(1, 2))).all()
+
+
+def test_nonphysical_state_is_reported():
+    op, hp = problems(2, "euler", 16, 16, bc=1)
+    U = I.random_state(op.shape, 3, eq=I.EULER)
+    U[3, 0, 8, 8] = -5.0   # negative energy
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, U)
+        with pytest.raises(H.HwenoError) as ei:
+            H.hweno_step(eng, sid)
+        assert ei.value.code == H.HWENO_ERR_NONPHYSICAL
+    finally:
+        H.hweno_destroy(eng)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_mixed_precision_stage(dim):
+    """FP32 bulk / FP64 weights: stage error against the FP64 oracle within 1e-5 of the
+    component scale.  Bound: FP32 unit roundoff u = 2^-24 = 6e-8; a point value is a sum of
+    stencil values with coefficients whose magnitudes add up to about 30 (Appendix), the
+    projection/unprojection and the Euler flux add a few roundings each, and the flux
+    difference enters the update scaled by dt/dx (< 1): about 160 u = 1e-5."""
+    if dim == 1:
+        op, hp = problems(1, "euler", 300, bc=1, precision=1)
+    else:
+        op, hp = problems(2, "euler", 200, 30, bc=1, precision=1)
+    for k in (1, 2, 3):
+        Uin, Un, Vh = _inputs(op, 40 + k)
+        if k == 1:
+            Un = Uin
+        alpha = O.alpha(op, Uin)
+        dx = (op.x1 - op.x0) / op.nx
+        dt = 0.3 * dx / alpha.sum()
+        ref, _, _ = O.stage(op, k, Uin, Un, Vh if k > 1 else None, alpha, dt)
+        got, _, _, st = gpu_stage(hp, k, Uin, Un, Vh, alpha, dt)
+        assert st == 0
+        e = rel_err(got, ref, Uin)
+        assert e <= 1e-5, f"stage {k}: {e:.3e}"
