@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark: cell-stage updates/s of the fused HWENO-U stage on 2D Euler 2048^2.
+
+Workload: 2D Euler (gamma = 1.4) on [0,1]^2, 2048 x 2048 cells, 3 moments per component,
+seeded 4-quadrant Riemann data (rho, p in [0.1, 2], u, v in [-1, 1]) with an isentropic
+vortex (seed 0 + rank), transmissive boundaries, CFL 0.6.  One bench step = one modified
+SSP-RK3 time step (dt kernel + three fused stage kernels) over the whole grid; value =
+cells * 3 * steps / seconds, timed with CUDA events on the engine's stream.
+
+Arms:
+  default            this library (FP64 path is the headline; the FP32-bulk/FP64-weights path
+                     is reported alongside with its L1/Linf deviation from the FP64 path)
+  --impl reference   the FP64 CPU oracle (a deliberately slow, serial C program) on bounded
+                     windows of the same workload, on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 2048
+METRIC = "cell-stage updates/s (2D Euler 2048^2, FP32 vs FP64 at stated L1 err); p50/p99 solve"
+UNIT = "cell-stage/s"
+# measured peaks (MEASURED_PEAKS.json holds HBM / bf16; FP64 and FP32 FMA rates were
+# measured on this machine's GB300 with an FMA-chain probe: 1.19 TFLOP/s FP64, 74 TFLOP/s FP32)
+FP64_PEAK_TFLOPS = 1.19
+FP32_PEAK_TFLOPS = 74.2
+# FP64 flops per cell-stage of the fused 2D Euler characteristic kernel, excluding the ring
+# redundancy: 2 x DFMA + DMUL + DADD thread instructions per launch from ncu on a 256^2 case
+# divided by the cells updated (profiles/stage2d_euler_fp64_2048.md)
+FP64_FLOPS_PER_CELL_STAGE = None
+ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
+
+
+def _dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _workload_config(n, extra=None):
+    cfg = {"workload": f"2D Euler quadrant+vortex {n}x{n}, 3 moments x 4 components, "
+                       f"transmissive, CFL 0.6, SSP-RK3 step = 3 fused stages",
+           "cells": n * n, "global_batch": 1, "seq_len": n * n, "parallelism": "replicas",
+           "l2": "inputs larger than L2 (state 402 MB per buffer), no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def run_reference(args):
+    """The FP64 oracle on the host cores: each step = one full SSP-RK3 step on a window of
+    the same seeded 2048^2 state (the oracle is serial)."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2402_03074_gb300 import inputs as I
+    win = args.ref_window
+    w = I.quadrant_vortex_2d(0, args.n, window=((args.n - win) // 2, (args.n - win) // 2, win, win))
+    op = O.Problem(dim=2, eq=O.EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1, y0=w.y0, y1=w.y1,
+                   bc=w.bc, cfl=0.6)
+    U = w.U0.copy()
+    t = 0.0
+    for _ in range(args.warmup):
+        U, t, _, _ = O.step(op, U, t)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, t, _, _ = O.step(op, U, t)
+    el = time.perf_counter() - t0
+    cs = w.nx * w.ny * 3 * args.steps
+    val = cs / el
+    sample = (f"{args.steps} SSP-RK3 steps of the serial FP64 C oracle on the central "
+              f"{win}x{win} window of the seeded {args.n}^2 state (same cell size)")
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": _workload_config(args.n),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline(n, seconds_target=15.0):
+    import oracle as O
+    from paper_2402_03074_gb300 import inputs as I
+    win = 128
+    w = I.quadrant_vortex_2d(0, n, window=((n - win) // 2, (n - win) // 2, win, win))
+    op = O.Problem(dim=2, eq=O.EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1, y0=w.y0, y1=w.y1,
+                   bc=w.bc, cfl=0.6)
+    U, t, steps = w.U0.copy(), 0.0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds_target:
+        U, t, _, _ = O.step(op, U, t)
+        steps += 1
+    el = time.perf_counter() - t0
+    return {"value": win * win * 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 steps of the serial FP64 C oracle on the central "
+                      f"{win}x{win} window of the seeded {n}^2 state ({el:.1f} s)"}
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+        torch.cuda.set_device(local)
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    from paper_2402_03074_gb300 import build as B
+    B.build()
+    from paper_2402_03074_gb300 import _binding as H
+    from paper_2402_03074_gb300 import inputs as I
+
+    n = args.n
+    w = I.quadrant_vortex_2d(rank, n)
+    U0 = w.U0
+    eng = H.hweno_create(device=dev)
+    stream = torch.cuda.ExternalStream(H.hweno_engine_stream(eng))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def prob(precision):
+        return H.make_problem(dim=2, equation=H.HWENO_EULER, nx=n, ny=n, x0=0.0, x1=1.0, y0=0.0,
+                              y1=1.0, bc=w.bc, cfl=0.6, precision=precision)
+
+    def timed_steps(precision, steps, warmup):
+        sid = H.hweno_open(eng, prob(precision), U0)
+        H.hweno_advance(eng, sid, math.inf, max_steps=warmup)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.hweno_advance(eng, sid, math.inf, max_steps=steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        barrier()
+        out = np.empty_like(U0)
+        H.hweno_get_state(eng, sid, out)
+        H.hweno_close(eng, sid)
+        return ms, out
+
+    # headline: FP64 path
+    with ClockSampler(dev) as clk:
+        ms64, out64 = timed_steps(H.HWENO_FP64, args.steps, args.warmup)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms64], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms64 = float(tt.item())
+    cell_stages = n * n * 3 * args.steps
+    value = world * cell_stages / (ms64 / 1e3)
+
+    # the fused stage kernel alone: per-launch duration from events on its stream
+    p64 = prob(H.HWENO_FP64)
+    d = torch.device("cuda", dev)
+    Ud = torch.from_numpy(U0).to(d)
+    Uo = torch.empty_like(Ud)
+    Vh = torch.zeros((4, 2, n, n), dtype=torch.float64, device=d)
+    a_in = torch.zeros(2, dtype=torch.float64, device=d)
+    H.hweno_alpha_device(p64, Ud, a_in, torch.cuda.current_stream().cuda_stream)
+    a_out = torch.zeros(2, dtype=torch.float64, device=d)
+    torch.cuda.synchronize()
+    dtv = 0.6 / ((a_in[0] + a_in[1]).item() * n)
+    dtt = torch.tensor([dtv], dtype=torch.float64, device=d)
+    st = torch.zeros(1, dtype=torch.int32, device=d)
+    ks = torch.cuda.Stream(device=d)
+    kernel_ms = []
+    with torch.cuda.stream(ks):
+        for rep in range(args.kernel_reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ks)
+            H.hweno_stage_device(p64, 1, Ud, Ud, Vh, Uo, a_in, a_out, dtt, st, ks.cuda_stream)
+            e1.record(ks)
+            e1.synchronize()
+            if rep > 0:
+                kernel_ms.append(e0.elapsed_time(e1))
+    k_ms = statistics.mean(kernel_ms)
+    del Ud, Uo, Vh
+
+    # FP32-bulk / FP64-weights path on identical inputs
+    mixed = None
+    if not args.no_mixed:
+        ms32, out32 = timed_steps(H.HWENO_MIXED32, args.steps, args.warmup)
+        diff = np.abs(out32[:, 0] - out64[:, 0])
+        scale = np.abs(out64[:, 0]).mean(axis=(1, 2))[:, None, None]
+        mixed = {"value": world * cell_stages / (ms32 / 1e3), "unit": UNIT, "dtype": "f32+f64",
+                 "ms_per_step": ms32 / args.steps,
+                 "l1_vs_fp64": float((diff / scale).mean()),
+                 "linf_vs_fp64": float((diff / scale).max()),
+                 "error_note": "relative to the mean |average| of each component, after the "
+                               "timed steps from identical inputs; FP64 path = oracle to 1e-12"}
+
+    # end to end through the C ABI with host buffers: per step H2D of the state from pinned
+    # memory, one step, D2H of the new state
+    e2e = None
+    if not args.no_e2e:
+        pin = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
+        pin[...] = U0
+        sid = H.hweno_open(eng, p64, pin)
+        H.hweno_step(eng, sid)
+        barrier()
+        t0 = time.perf_counter()
+        tsim = 0.0
+        for _ in range(args.e2e_steps):
+            H.hweno_set_state(eng, sid, pin, tsim)
+            H.hweno_step(eng, sid)
+            _, tsim = H.hweno_get_state(eng, sid, pin)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        H.hweno_close(eng, sid)
+        e2e = {"value": world * n * n * 3 * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes),
+               "steps": args.e2e_steps}
+    H.hweno_destroy(eng)
+
+    if rank != 0:
+        return
+    flops = FP64_FLOPS_PER_CELL_STAGE
+    achieved = flops * n * n / (k_ms / 1e3) / 1e12 if flops else None
+    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                "kernel": "stage2d_kernel<EULER, characteristic, double>",
+                "kernel_ms": k_ms, "flops_per_cell_stage": flops,
+                "hbm_GBps": ALGO_BYTES_PER_CELL_STAGE * n * n / (k_ms / 1e3) / 1e9,
+                "peak_note": "FP64 FMA rate measured on this pool's GB300 (of measured)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": _workload_config(n), "gpu_launches": 4 * args.steps,
+            "clocks": clk.summary(), "roofline": roofline, "mixed32": mixed, "e2e": e2e}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds)
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--kernel-reps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-window", type=int, default=128)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,131 @@
+// batch.cu -- batched, persistent HWENO-U stage launches over many 2D solves.
+//
+// All live solves of one kernel class (equation, characteristic decomposition) are advanced
+// by one launch per RK stage.  The launch is persistent (one block per resident slot); its
+// blocks take work items from a device counter.  An item is one (band, row chunk) of one
+// solve, exactly the unit of the single-solve kernel, so uneven grids share the GPU and the
+// load balances at item granularity.  FP64 and FP32-bulk solves share the launch (the item
+// branches on the solve's precision).  Every solve keeps its own scalars (dt, t, LF speeds,
+// status); one thread per solve advances them at the start of each step, so each solve
+// steps with its own dt.  The work lists live in device memory: admission and retirement
+// rewrite them between steps and the captured step graph stays valid.
+#include "batch.h"
+#include "stage2d_item.cuh"
+
+namespace hw {
+
+__global__ void batch_dt_kernel(BatchDt* d, BatchCtl* ctl, int nctl) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < d->n) dt_update(d->sc[s], d->inv_dx[s], d->inv_dy[s], d->dim[s]);
+  if (s < nctl) {
+    ctl[s].next[0] = 0u;
+    ctl[s].next[1] = 0u;
+    ctl[s].next[2] = 0u;
+  }
+}
+
+template <int EQ, bool CHAR, int BW>
+__global__ void __launch_bounds__(BW, 1) batch_stage_kernel(const BatchSolve* bs, BatchCtl* ctl,
+                                                            int k) {
+  extern __shared__ double smem[];
+  __shared__ double red[2][BW / 32];
+  __shared__ int item_s;
+  const int n_items = ctl->n_items, n_solves = ctl->n_solves;
+#pragma unroll 1
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (int)atomicAdd(&ctl->next[k - 1], 1u);
+    __syncthreads();
+    const int item = item_s;
+    __syncthreads();
+    if (item >= n_items) break;
+    // the solve owning the item: last solve with item_base <= item
+    int lo = 0, hi = n_solves - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (bs[mid].item_base <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchSolve& B = bs[lo];
+    if (*(volatile const int*)&B.sc->active == 0) continue;  // uniform over the block
+    const int local = item - B.item_base;
+    const int band = local % B.bands, chunk = local / B.bands;
+    KStage S;
+    S.Uin = B.U[k - 1];
+    S.Un = B.U[0];
+    S.Vh = B.Vh;
+    S.Uout = B.U[k % 3];
+    S.alpha_in = B.sc->alpha[k - 1];
+    S.alpha_out = B.sc->alpha[k];
+    S.dt = &B.sc->dt;
+    S.status = &B.sc->status;
+    S.active = &B.sc->active;
+    S.k = k;
+    if (B.mixed) stage2d_item<EQ, CHAR, float, BW>(B.P, S, band, chunk, B.rows, B.wout, smem, red);
+    else stage2d_item<EQ, CHAR, double, BW>(B.P, S, band, chunk, B.rows, B.wout, smem, red);
+  }
+}
+
+template <int EQ, bool CHAR>
+static cudaError_t launch_batch_t(const BatchSolve* bs, BatchCtl* ctl, int k, cudaStream_t st,
+                                  int* slots_out) {
+  constexpr int BW = kBatchBW;
+  const size_t smem = smem_bytes2d<EQ, double, BW>();  // >= the float variant
+  auto kern = batch_stage_kernel<EQ, CHAR, BW>;
+  static int slots = 0;
+  if (slots == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BW, smem);
+    if (e != cudaSuccess) return e;
+    slots = (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
+  }
+  if (slots_out) *slots_out = slots;
+  if (!bs) return cudaSuccess;  // query only
+  kern<<<slots, BW, smem, st>>>(bs, ctl, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,
+                               cudaStream_t st) {
+  switch (cls) {
+    case 0: return launch_batch_t<EQ_ADV, false>(bs, ctl, k, st, nullptr);
+    case 1: return launch_batch_t<EQ_BURG, false>(bs, ctl, k, st, nullptr);
+    case 2: return launch_batch_t<EQ_EULER, false>(bs, ctl, k, st, nullptr);
+    default: return launch_batch_t<EQ_EULER, true>(bs, ctl, k, st, nullptr);
+  }
+}
+
+cudaError_t prepare_batch_stage(int cls) {
+  switch (cls) {
+    case 0: return launch_batch_t<EQ_ADV, false>(nullptr, nullptr, 1, 0, nullptr);
+    case 1: return launch_batch_t<EQ_BURG, false>(nullptr, nullptr, 1, 0, nullptr);
+    case 2: return launch_batch_t<EQ_EULER, false>(nullptr, nullptr, 1, 0, nullptr);
+    default: return launch_batch_t<EQ_EULER, true>(nullptr, nullptr, 1, 0, nullptr);
+  }
+}
+
+int batch_class(int equation, int characteristic) {
+  if (equation == EQ_ADV) return 0;
+  if (equation == EQ_BURG) return 1;
+  return characteristic ? 3 : 2;
+}
+
+cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st) {
+  const int n = cap > nctl ? cap : nctl;
+  batch_dt_kernel<<<(n + 127) / 128, 128, 0, st>>>(d, ctl, nctl);
+  return cudaGetLastError();
+}
+
+void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks) {
+  constexpr int BW = kBatchBW;
+  *bands = (nx + (BW - 2) - 1) / (BW - 2);
+  *wout = (nx + *bands - 1) / *bands;
+  if (rows < 1) rows = 1;
+  *chunks = (ny + rows - 1) / rows;
+}
+
+}  // namespace hw

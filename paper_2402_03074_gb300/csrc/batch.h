@@ -1,0 +1,47 @@
+// batch.h -- device work lists of the batched persistent stage launches (batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace hw {
+
+constexpr int kBatchBW = 128;     // threads per block of the batched stage kernel
+constexpr int kBatchClasses = 4;  // advection, Burgers, Euler component-wise, Euler characteristic
+
+// One solve in a batch (device-resident array, rewritten on admission / retirement).
+struct BatchSolve {
+  KProblem P;
+  double* U[3];        // U^n, U^(1), U^(2)
+  double* Vh;
+  DevScal* sc;
+  int mixed;           // 1: FP32 bulk / FP64 weights
+  int bands, wout, rows, chunks;
+  int item_base;       // first work item of the solve
+};
+
+// Control block of one class's launches.
+struct BatchCtl {
+  int n_solves;
+  int n_items;
+  unsigned int next[3];  // work counters of the three stage launches of a step
+};
+
+// Per-solve step scalars of every solve in the batch (all classes).
+constexpr int kBatchCap = 1024;
+struct BatchDt {
+  int n;       // solves whose step starts here (the batched ones, first in the list)
+  int n_all;   // all live solves (the gather of their scalars)
+  DevScal* sc[kBatchCap];
+  double inv_dx[kBatchCap], inv_dy[kBatchCap];
+  int dim[kBatchCap];
+};
+
+int batch_class(int equation, int characteristic);
+void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks);
+cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st);
+cudaError_t prepare_batch_stage(int cls);  // function attributes / occupancy, no launch
+cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,
+                               cudaStream_t st);
+
+}  // namespace hw

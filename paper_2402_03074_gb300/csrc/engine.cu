@@ -31,53 +31,9 @@
 
 namespace hw {
 
-// ------------------------------------------------------------------------------------
-// device scalars of a solve
-struct DevScal {
-  double alpha[4][2];  // [3]: speeds of U^n (from the previous step / open), [0..2]: stage inputs
-  double dt;
-  double t;
-  double t_end;
-  double dt_fixed;
-  double cfl;
-  long long steps;
-  long long step_limit;
-  int active;
-  uint32_t status;
-};
-
 __global__ void dt_kernel(DevScal* s, double inv_dx, double inv_dy, int dim) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double a0 = s->alpha[3][0], a1 = s->alpha[3][1];
-  s->alpha[0][0] = a0;
-  s->alpha[0][1] = a1;
-  s->alpha[1][0] = s->alpha[1][1] = 0.0;
-  s->alpha[2][0] = s->alpha[2][1] = 0.0;
-  s->alpha[3][0] = s->alpha[3][1] = 0.0;
-  const double t = s->t, te = s->t_end;
-  if (!(t < te) || s->steps >= s->step_limit || s->status != 0u) {
-    s->active = 0;
-    s->dt = 0.0;
-    s->alpha[3][0] = a0;  // keep the speeds of the (unchanged) state
-    s->alpha[3][1] = a1;
-    return;
-  }
-  double dt;
-  if (s->dt_fixed > 0.0) {
-    dt = s->dt_fixed;
-  } else {
-    const double rate = a0 * inv_dx + (dim == 2 ? a1 * inv_dy : 0.0);
-    dt = (rate > 0.0) ? s->cfl / rate : te - t;
-  }
-  double tn = t + dt;
-  if (!(tn < te)) {  // clip the last step onto t_end
-    dt = te - t;
-    tn = te;
-  }
-  s->dt = dt;
-  s->t = tn;
-  s->steps += 1;
-  s->active = 1;
+  dt_update(s, inv_dx, inv_dy, dim);
 }
 
 // wave speeds of a state: max |f'| and |g'| over the cell averages
@@ -489,6 +445,15 @@ int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps,
 }
 
 double solve_time(Solve* s) { return s->host->t; }
+DevScal* solve_scalars(Solve* s) { return s->sc; }
+void solve_pointers(Solve* s, double** U0, double** U1, double** U2, double** Vh) {
+  *U0 = s->U0;
+  *U1 = s->U1;
+  *U2 = s->U2;
+  *Vh = s->Vh;
+}
+const hweno_problem* solve_problem(Solve* s) { return &s->prob; }
+KProblem solve_kproblem(Solve* s) { return s->kp; }
 int solve_copy_out(hweno_engine* e, Solve* s, double* host) {
   CUDA_TRY(e, cudaMemcpyAsync(host, s->U0, sizeof(double) * s->nU, cudaMemcpyDeviceToHost,
                               e->stream));

@@ -74,7 +74,11 @@ __device__ __forceinline__ double mirror_sign(int c, int m, int fx, int fy) {
 }
 
 // ---------------------------------------------------------------------------------------
-// nonlinear weights (Eq. 2.10-2.11 / 2.21-2.22), double precision
+// nonlinear weights (Eq. 2.10-2.11 / 2.21-2.22), double precision.
+// w~_m = gamma_m (1 + tau/d_m) with d_m = beta_m u_ave + eps > 0; the normalised weights are
+// formed with a single reciprocal: omega_m = gamma_m (D + tau D_m) / sum_k gamma_k (D + tau D_k)
+// with D = prod_k d_k and D_m = prod_{k != m} d_k (equal to the direct formula in exact
+// arithmetic).  If the products leave the normal double range the direct formula is used.
 template <int NS>
 __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], double uave,
                                                   const KProblem& P, double (&om)[NS]) {
@@ -85,19 +89,65 @@ __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], doub
   const double tau = s * s;
   const double ua = (P.wmode == 1) ? 1.0 : uave;
   const double g0 = 1.0 - (double)(NS - 1) * P.glo;
-  double wt[NS];
+  double d[NS];
+#pragma unroll
+  for (int m = 0; m < NS; ++m) d[m] = fma(beta[m], ua, P.eps);
+  // prefix / suffix products
+  double pre[NS + 1], suf[NS + 1];
+  pre[0] = 1.0;
+  suf[NS] = 1.0;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) pre[m + 1] = (m == 0) ? d[0] : pre[m] * d[m];
+#pragma unroll
+  for (int m = NS - 1; m >= 0; --m) suf[m] = (m == NS - 1) ? d[NS - 1] : suf[m + 1] * d[m];
+  const double D = pre[NS];
+  double N[NS];
   double sum = 0.0;
 #pragma unroll
   for (int m = 0; m < NS; ++m) {
-    const double gm = (m == 0) ? g0 : P.glo;
-    const double d = fma(beta[m], ua, P.eps);
-    wt[m] = fma(gm, tau / d, gm);
-    sum += wt[m];
+    const double Dm = (m == 0) ? suf[1] : ((m == NS - 1) ? pre[NS - 1] : pre[m] * suf[m + 1]);
+    N[m] = ((m == 0) ? g0 : P.glo) * fma(tau, Dm, D);
+    sum += N[m];
   }
-  const double inv = 1.0 / sum;
+  // exponent checks on the INT pipe: D and the sum must be normal and far from overflow
+  const long long eD = (__double_as_longlong(D) >> 52) & 0x7ff;
+  const long long eS = (__double_as_longlong(sum) >> 52) & 0x7ff;
+  if (eD > 64 && eD < 2047 - 64 && eS > 64 && eS < 2047 - 64) {
+    const double inv = 1.0 / sum;
 #pragma unroll
-  for (int m = 0; m < NS; ++m) om[m] = wt[m] * inv;
+    for (int m = 0; m < NS; ++m) om[m] = N[m] * inv;
+  } else {
+    double wt[NS];
+    double ws = 0.0;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) {
+      const double gm = (m == 0) ? g0 : P.glo;
+      wt[m] = fma(gm, tau / d[m], gm);
+      ws += wt[m];
+    }
+    const double inv = 1.0 / ws;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) om[m] = wt[m] * inv;
+  }
 }
+
+// Reciprocal 1/x: Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
+// seeded with the single-precision reciprocal of x; two steps take the 2^-22 relative error
+// of the seed below 2^-52 (result within 1 ulp of 1/x).  Values whose exponent is outside
+// +-100 of 1 (where the float seed could over- or underflow) use the division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const long long eb = (__double_as_longlong(x) >> 52) & 0x7ff;
+  if (eb < 1023 - 100 || eb > 1023 + 100) return 1.0 / x;
+  double y = (double)__frcp_rn((float)x);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+template <typename R>
+__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ double rcp<double>(double x) { return rcp_nr(x); }
 
 // ---------------------------------------------------------------------------------------
 // 1D reconstruction of one field (Sec. 2.1 Steps 1-3, Eq. 2.12).
@@ -380,13 +430,13 @@ template <int DIM, typename R>
 __device__ __forceinline__ void euler_flux(const KProblem& P, int dir, const R* u, R* f) {
   const R gm1 = (R)(P.gam - 1.0);
   if (DIM == 1) {
-    const R vel = u[1] / u[0];
+    const R vel = u[1] * rcp<R>(u[0]);
     const R p = gm1 * (u[2] - R(0.5) * u[1] * vel);
     f[0] = u[1];
     f[1] = u[1] * vel + p;
     f[2] = vel * (u[2] + p);
   } else {
-    const R ir = R(1) / u[0];
+    const R ir = rcp<R>(u[0]);
     const R vx = u[1] * ir, vy = u[2] * ir;
     const R p = gm1 * (u[3] - R(0.5) * (u[1] * vx + u[2] * vy));
     if (dir == 0) {

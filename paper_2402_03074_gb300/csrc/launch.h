@@ -6,6 +6,56 @@
 
 namespace hw {
 
+// Device-resident scalars of a solve.
+struct DevScal {
+  double alpha[4][2];  // [3]: LF speeds of U^n (previous step / open); [0..2]: stage inputs
+  double dt;
+  double t;
+  double t_end;
+  double dt_fixed;
+  double cfl;
+  long long steps;
+  long long step_limit;
+  int active;
+  uint32_t status;
+};
+
+// Start of a time step (one thread): Delta t from the LF speeds of U^n (CFL rule, R8
+// reading) or the fixed step, clipped to t_end; clears the speed slots the three stages
+// raise; sets `active` (0 once t_end, the step limit or a bad status is reached).
+__device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_dy, int dim) {
+  const double a0 = s->alpha[3][0], a1 = s->alpha[3][1];
+  s->alpha[0][0] = a0;
+  s->alpha[0][1] = a1;
+  s->alpha[1][0] = s->alpha[1][1] = 0.0;
+  s->alpha[2][0] = s->alpha[2][1] = 0.0;
+  s->alpha[3][0] = s->alpha[3][1] = 0.0;
+  const double t = s->t, te = s->t_end;
+  if (!(t < te) || s->steps >= s->step_limit || s->status != 0u) {
+    s->active = 0;
+    s->dt = 0.0;
+    s->alpha[3][0] = a0;  // the state is unchanged: keep its speeds
+    s->alpha[3][1] = a1;
+    return;
+  }
+  double dt;
+  if (s->dt_fixed > 0.0) {
+    dt = s->dt_fixed;
+  } else {
+    const double rate = a0 * inv_dx + (dim == 2 ? a1 * inv_dy : 0.0);
+    dt = (rate > 0.0) ? s->cfl / rate : te - t;
+  }
+  double tn = t + dt;
+  if (!(tn < te)) {  // clip the last step onto t_end
+    dt = te - t;
+    tn = te;
+  }
+  s->dt = dt;
+  s->t = tn;
+  s->steps += 1;
+  s->active = 1;
+}
+
 // One stage of the modified SSP-RK3 over a whole grid (1D / 2D), asynchronous on st.
 cudaError_t launch_stage1d(int eq, bool characteristic, bool mixed, const KProblem& P,
                            const KStage& S, cudaStream_t st);

@@ -1,13 +1,32 @@
-// server.cu -- served path: queue, admission by device memory, advance of all live solves.
+// server.cu -- served path: continuous batching of solves.
+//
+// hweno_submit queues a request (the initial moments are copied at the call).  The serving
+// loop (hweno_serve on the caller's thread, or a background thread when the engine was
+// created with server_thread = 1) repeatedly
+//   1. admits queued requests while the device-memory budget and the slot table allow
+//      (allocation, upload, speeds of the initial state, entry in the device work lists);
+//   2. advances every live solve by a few time steps: one replay of a captured step graph =
+//      one batched dt launch (each solve its own dt) + per kernel class three persistent
+//      stage launches over the work items of all live 2D solves of that class (1D solves
+//      are advanced by their own step graph);
+//   3. reads the scalars of all live solves back in one copy and retires the finished ones
+//      (result copied to host memory, device memory released, work lists rewritten).
+// Requests that arrive while others run are admitted at the next iteration: their work
+// overlaps with the running solves inside the same launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/hweno.h"
+#include "batch.h"
 #include "server.h"
 
 namespace hw {
@@ -15,7 +34,7 @@ namespace hw {
 struct Request {
   uint64_t ticket;
   hweno_problem prob;
-  std::vector<double> init;   // host copy of the initial moments
+  std::vector<double> init;  // host copy of the initial moments (until admission)
   Solve* solve = nullptr;
   int status = HWENO_PENDING;
   double t = 0.0;
@@ -25,61 +44,304 @@ struct Request {
 };
 
 struct Server {
-  hweno_engine* eng;
-  std::deque<Request*> queue;      // waiting for admission
-  std::vector<Request*> live;      // admitted, running
+  hweno_engine* eng = nullptr;
+  std::deque<Request*> queue;
+  std::vector<Request*> live;
   std::map<uint64_t, Request*> all;
   uint64_t next_ticket = 1;
+  // device work lists
+  BatchSolve* d_bs = nullptr;   // [kBatchClasses][kBatchCap]
+  BatchCtl* d_ctl = nullptr;    // [kBatchClasses]
+  BatchDt* d_dt = nullptr;
+  BatchDt* h_dt = nullptr;      // pinned staging
+  BatchSolve* h_bs = nullptr;   // pinned staging [kBatchClasses][kBatchCap]
+  BatchCtl* h_ctl = nullptr;    // pinned staging
+  DevScal* d_gather = nullptr;  // [kBatchCap] scalars of the live solves
+  DevScal* h_gather = nullptr;  // pinned
+  cudaGraphExec_t graph = nullptr;
+  unsigned graph_classes = 0;   // bit mask of the classes the graph launches
+  bool dirty = true;
+  int rows = 32;                // rows per work item
+  // background thread
+  std::thread worker;
+  std::atomic<bool> stop{false};
+  std::condition_variable_any cv;
+  bool threaded = false;
 };
 
-Server* server_create(hweno_engine* e, int) {
+double solve_time(Solve* s);
+int solve_copy_out(hweno_engine* e, Solve* s, double* host);
+DevScal* solve_scalars(Solve* s);
+void solve_pointers(Solve* s, double** U0, double** U1, double** U2, double** Vh);
+const hweno_problem* solve_problem(Solve* s);
+KProblem solve_kproblem(Solve* s);
+
+__global__ void gather_scalars_kernel(BatchDt* d, DevScal* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < d->n_all) out[s] = *d->sc[s];
+}
+
+static int server_alloc(Server* S) {
+  cudaError_t c = cudaSuccess;
+  if (c == cudaSuccess) c = cudaMalloc(&S->d_bs, sizeof(BatchSolve) * kBatchClasses * kBatchCap);
+  if (c == cudaSuccess) c = cudaMalloc(&S->d_ctl, sizeof(BatchCtl) * kBatchClasses);
+  if (c == cudaSuccess) c = cudaMalloc(&S->d_dt, sizeof(BatchDt));
+  if (c == cudaSuccess) c = cudaMallocHost(&S->h_dt, sizeof(BatchDt));
+  if (c == cudaSuccess) c = cudaMallocHost(&S->h_bs, sizeof(BatchSolve) * kBatchClasses * kBatchCap);
+  if (c == cudaSuccess) c = cudaMallocHost(&S->h_ctl, sizeof(BatchCtl) * kBatchClasses);
+  if (c == cudaSuccess) c = cudaMalloc(&S->d_gather, sizeof(DevScal) * kBatchCap);
+  if (c == cudaSuccess) c = cudaMallocHost(&S->h_gather, sizeof(DevScal) * kBatchCap);
+  if (c != cudaSuccess) {
+    cudaGetLastError();
+    return HWENO_ERR_OOM;
+  }
+  std::memset(S->h_ctl, 0, sizeof(BatchCtl) * kBatchClasses);
+  std::memset(S->h_dt, 0, sizeof(BatchDt));
+  return HWENO_OK;
+}
+
+static void server_free(Server* S) {
+  if (S->graph) cudaGraphExecDestroy(S->graph);
+  cudaFree(S->d_bs);
+  cudaFree(S->d_ctl);
+  cudaFree(S->d_dt);
+  cudaFreeHost(S->h_dt);
+  cudaFreeHost(S->h_bs);
+  cudaFreeHost(S->h_ctl);
+  cudaFree(S->d_gather);
+  cudaFreeHost(S->h_gather);
+}
+
+static bool batched(const hweno_problem* p) { return p->dim == 2; }
+
+// rewrite the device work lists from the live set (batched 2D solves first: the dt list
+// covers them, the gather list covers every live solve in the same order as S->live)
+static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
+  std::stable_partition(S->live.begin(), S->live.end(),
+                        [](Request* r) { return batched(&r->prob); });
+  int nb[kBatchClasses] = {0, 0, 0, 0};
+  int items[kBatchClasses] = {0, 0, 0, 0};
+  int n = 0, nall = 0;
+  *classes = 0;
+  for (Request* r : S->live) {
+    Solve* sv = r->solve;
+    const hweno_problem* p = solve_problem(sv);
+    KProblem kp = solve_kproblem(sv);
+    S->h_dt->sc[nall] = solve_scalars(sv);
+    S->h_dt->inv_dx[nall] = kp.inv_dx;
+    S->h_dt->inv_dy[nall] = kp.inv_dy;
+    S->h_dt->dim[nall] = p->dim;
+    ++nall;
+    if (!batched(p)) continue;
+    ++n;
+    const int cls = batch_class(p->equation, p->characteristic);
+    BatchSolve& B = S->h_bs[cls * kBatchCap + nb[cls]];
+    B.P = kp;
+    solve_pointers(sv, &B.U[0], &B.U[1], &B.U[2], &B.Vh);
+    B.sc = solve_scalars(sv);
+    B.mixed = p->precision == HWENO_MIXED32;
+    B.rows = S->rows;
+    batch_geometry(p->nx, p->ny, S->rows, &B.bands, &B.wout, &B.chunks);
+    B.item_base = items[cls];
+    items[cls] += B.bands * B.chunks;
+    ++nb[cls];
+    *classes |= 1u << cls;
+  }
+  S->h_dt->n = n;
+  S->h_dt->n_all = nall;
+  for (int c = 0; c < kBatchClasses; ++c) {
+    S->h_ctl[c].n_solves = nb[c];
+    S->h_ctl[c].n_items = items[c];
+    S->h_ctl[c].next[0] = S->h_ctl[c].next[1] = S->h_ctl[c].next[2] = 0u;
+    if (nb[c])
+      if (cudaMemcpyAsync(S->d_bs + c * kBatchCap, S->h_bs + c * kBatchCap,
+                          sizeof(BatchSolve) * nb[c], cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return HWENO_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(BatchCtl) * kBatchClasses,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HWENO_ERR_CUDA;
+  if (cudaMemcpyAsync(S->d_dt, S->h_dt, sizeof(BatchDt), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HWENO_ERR_CUDA;
+  // the staging buffers are pinned and rewritten only here: finish the copies first
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HWENO_ERR_CUDA;
+  return HWENO_OK;
+}
+
+// one step of every live batched solve
+static cudaError_t enqueue_batch_step(Server* S, unsigned classes, cudaStream_t st) {
+  cudaError_t e = launch_batch_dt(S->d_dt, S->d_ctl, kBatchClasses, kBatchCap, st);
+  for (int k = 1; k <= 3 && e == cudaSuccess; ++k)
+    for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c)
+      if (classes & (1u << c)) e = launch_batch_stage(c, S->d_bs + c * kBatchCap, S->d_ctl + c, k, st);
+  return e;
+}
+
+static int ensure_batch_graph(Server* S, unsigned classes, cudaStream_t st) {
+  if (S->graph && S->graph_classes == classes) return HWENO_OK;
+  if (S->graph) {
+    cudaGraphExecDestroy(S->graph);
+    S->graph = nullptr;
+  }
+  // set the launch configuration (function attributes, occupancy) outside the capture
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c)
+    if (classes & (1u << c)) e = prepare_batch_stage(c);
+  if (e != cudaSuccess) return HWENO_ERR_CUDA;
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return HWENO_ERR_CUDA;
+  const int G = 2;  // steps per graph
+  for (int s = 0; s < G && e == cudaSuccess; ++s) e = enqueue_batch_step(S, classes, st);
+  cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) return HWENO_ERR_CUDA;
+  e = cudaGraphInstantiate(&S->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return HWENO_ERR_CUDA;
+  S->graph_classes = classes;
+  return HWENO_OK;
+}
+
+static void finish(Server* S, Request* r, int rc) {
+  r->t = solve_time(r->solve);
+  if (rc == HWENO_OK) {
+    const size_t n = (size_t)r->prob.nx * r->prob.ny * hweno_ncomp(&r->prob) * hweno_nmom(&r->prob);
+    r->result.resize(n);
+    rc = solve_copy_out(S->eng, r->solve, r->result.data());
+  }
+  engine_release_solve(S->eng, r->solve);
+  r->solve = nullptr;
+  r->status = rc;
+  r->t_finish = now_seconds();
+}
+
+static void admit(Server* S, cudaStream_t st) {
+  while (!S->queue.empty() && (int)S->live.size() < std::min(engine_max_slots(S->eng), kBatchCap)) {
+    Request* r = S->queue.front();
+    if (solve_bytes(&r->prob) > engine_budget_left(S->eng)) break;
+    Solve* sv = nullptr;
+    int rc = engine_alloc_solve(S->eng, &r->prob, &sv);
+    if (rc == HWENO_ERR_BUSY || rc == HWENO_ERR_OOM) break;  // wait for memory to free up
+    S->queue.pop_front();
+    if (rc) {
+      r->status = rc;
+      r->t_finish = now_seconds();
+      continue;
+    }
+    rc = engine_load_state(S->eng, sv, r->init.data(), 0.0, st);
+    if (rc == HWENO_OK) rc = engine_set_target(S->eng, sv, r->prob.t_end, 1LL << 62, st);
+    if (rc) {
+      engine_release_solve(S->eng, sv);
+      r->status = rc;
+      r->t_finish = now_seconds();
+      continue;
+    }
+    r->solve = sv;
+    r->t_admit = now_seconds();
+    std::vector<double>().swap(r->init);
+    S->live.push_back(r);
+    S->dirty = true;
+  }
+}
+
+// one serving iteration: admit, advance up to max_steps steps, retire
+static int serve_once(Server* S, long long max_steps) {
+  hweno_engine* e = S->eng;
+  cudaStream_t st = engine_stream(e);
+  admit(S, st);
+  if (S->live.empty()) return HWENO_OK;
+  if (S->dirty) {
+    unsigned classes = 0;
+    int rc = rebuild_lists(S, st, &classes);
+    if (rc) return rc;
+    S->dirty = false;
+    if (classes) {
+      rc = ensure_batch_graph(S, classes, st);
+      if (rc) return rc;
+    }
+  }
+  // 1D solves: their own step graphs
+  for (Request* r : S->live)
+    if (!batched(&r->prob)) {
+      long long n = 0;
+      engine_run(e, r->solve, r->prob.t_end, max_steps, &n);
+    }
+  bool any2d = false;
+  for (Request* r : S->live) any2d |= batched(&r->prob);
+  if (any2d) {
+    const long long reps = std::max<long long>(1, max_steps / 2);
+    for (long long i = 0; i < reps; ++i)
+      if (cudaGraphLaunch(S->graph, st) != cudaSuccess) return HWENO_ERR_CUDA;
+  }
+  // scalars of all live solves in one copy
+  const int n = S->h_dt->n_all;
+  gather_scalars_kernel<<<(n + 127) / 128, 128, 0, st>>>(S->d_dt, S->d_gather);
+  if (cudaMemcpyAsync(S->h_gather, S->d_gather, sizeof(DevScal) * n, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return HWENO_ERR_CUDA;
+  std::vector<Request*> still;
+  for (size_t q = 0; q < S->live.size(); ++q) {
+    Request* r = S->live[q];
+    const DevScal& d = S->h_gather[q];
+    r->t = d.t;
+    r->steps = d.steps;
+    if (d.status) {
+      finish(S, r, HWENO_ERR_NONPHYSICAL);
+      S->dirty = true;
+    } else if (!(d.t < r->prob.t_end)) {
+      engine_read_scalars(e, r->solve, st);
+      finish(S, r, HWENO_OK);
+      S->dirty = true;
+    } else {
+      still.push_back(r);
+    }
+  }
+  S->live.swap(still);
+  return HWENO_OK;
+}
+
+static void worker_loop(Server* S) {
+  std::recursive_mutex& mu = engine_mutex(S->eng);
+  while (!S->stop.load()) {
+    std::unique_lock<std::recursive_mutex> lk(mu);
+    if (S->live.empty() && S->queue.empty()) {
+      S->cv.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    cudaSetDevice(engine_device(S->eng));
+    serve_once(S, 8);
+  }
+}
+
+Server* server_create(hweno_engine* e, int with_thread) {
   Server* s = new Server();
   s->eng = e;
+  if (server_alloc(s) != HWENO_OK) {
+    server_free(s);
+    delete s;
+    return nullptr;
+  }
+  if (with_thread) {
+    s->threaded = true;
+    s->worker = std::thread(worker_loop, s);
+  }
   return s;
 }
 
 void server_destroy(Server* s) {
   if (!s) return;
+  if (s->threaded) {
+    s->stop.store(true);
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+  }
   for (auto& kv : s->all) {
     if (kv.second->solve) engine_release_solve(s->eng, kv.second->solve);
     delete kv.second;
   }
+  server_free(s);
   delete s;
-}
-
-static void admit(Server* s) {
-  while (!s->queue.empty() && (int)s->live.size() < engine_max_slots(s->eng)) {
-    Request* r = s->queue.front();
-    if (solve_bytes(&r->prob) > engine_budget_left(s->eng)) break;
-    Solve* sv = nullptr;
-    int rc = engine_alloc_solve(s->eng, &r->prob, &sv);
-    if (rc == HWENO_ERR_BUSY) break;
-    s->queue.pop_front();
-    if (rc) { r->status = rc; r->t_finish = now_seconds(); continue; }
-    rc = engine_load_state(s->eng, sv, r->init.data(), 0.0, engine_stream(s->eng));
-    if (rc) { engine_release_solve(s->eng, sv); r->status = rc; r->t_finish = now_seconds(); continue; }
-    r->solve = sv;
-    r->t_admit = now_seconds();
-    r->init.clear();
-    r->init.shrink_to_fit();
-    s->live.push_back(r);
-  }
-}
-
-double solve_time(Solve* s);
-int solve_copy_out(hweno_engine* e, Solve* s, double* host);
-
-static void finish(Server* s, Request* r, int rc) {
-  r->t = solve_time(r->solve);
-  if (rc == HWENO_OK) {
-    const size_t n = (size_t)r->prob.nx * r->prob.ny * hweno_ncomp(&r->prob) * hweno_nmom(&r->prob);
-    r->result.resize(n);
-    rc = solve_copy_out(s->eng, r->solve, r->result.data());
-  }
-  engine_release_solve(s->eng, r->solve);
-  r->solve = nullptr;
-  r->status = rc;
-  r->t_finish = now_seconds();
 }
 
 }  // namespace hw
@@ -92,10 +354,17 @@ int hweno_submit(hweno_engine* e, const hweno_problem* p, const double* host, ui
   if (!e || !p || !host || !ticket) return HWENO_ERR_ARG;
   std::string why;
   int rc = problem_check(p, &why);
-  if (rc) { engine_set_error(e, why); return rc; }
-  if (!(p->t_end > 0.0)) { engine_set_error(e, "t_end must be > 0"); return HWENO_ERR_ARG; }
+  if (rc) {
+    engine_set_error(e, why);
+    return rc;
+  }
+  if (!(p->t_end > 0.0)) {
+    engine_set_error(e, "t_end must be > 0");
+    return HWENO_ERR_ARG;
+  }
   std::lock_guard<std::recursive_mutex> lk(engine_mutex(e));
   Server* s = engine_server(e);
+  if (!s) return HWENO_ERR_STATE;
   Request* r = new Request();
   r->ticket = s->next_ticket++;
   r->prob = *p;
@@ -105,39 +374,32 @@ int hweno_submit(hweno_engine* e, const hweno_problem* p, const double* host, ui
   s->queue.push_back(r);
   s->all[r->ticket] = r;
   *ticket = r->ticket;
+  s->cv.notify_all();
   return HWENO_OK;
 }
 
 int hweno_serve(hweno_engine* e, int64_t max_steps, int* active) {
   if (!e) return HWENO_ERR_ARG;
   std::lock_guard<std::recursive_mutex> lk(engine_mutex(e));
-  cudaSetDevice(engine_device(e));
   Server* s = engine_server(e);
-  admit(s);
-  std::vector<Request*> still;
-  for (Request* r : s->live) {
-    long long st = 0;
-    int rc = engine_run(e, r->solve, r->prob.t_end, max_steps, &st);
-    r->steps += st;
-    bool done = rc != HWENO_OK;
-    if (!done) {
-      rc = engine_read_scalars(e, r->solve, engine_stream(e));
-      done = rc != HWENO_OK || !(solve_time(r->solve) < r->prob.t_end);
-    }
-    if (done) finish(s, r, rc);
-    else still.push_back(r);
-  }
-  s->live.swap(still);
-  if (active) *active = (int)s->live.size();
-  return HWENO_OK;
+  if (!s) return HWENO_ERR_STATE;
+  cudaSetDevice(engine_device(e));
+  int rc = serve_once(s, max_steps < 1 ? 1 : max_steps);
+  if (active) *active = (int)(s->live.size() + s->queue.size());
+  if (rc) engine_set_error(e, "serving iteration failed");
+  return rc;
 }
 
 int hweno_poll(hweno_engine* e, uint64_t ticket, double* out, hweno_result* info) {
   if (!e) return HWENO_ERR_ARG;
   std::lock_guard<std::recursive_mutex> lk(engine_mutex(e));
   Server* s = engine_server(e);
+  if (!s) return HWENO_ERR_STATE;
   auto it = s->all.find(ticket);
-  if (it == s->all.end()) return HWENO_ERR_ARG;
+  if (it == s->all.end()) {
+    engine_set_error(e, "unknown or retired ticket");
+    return HWENO_ERR_ARG;
+  }
   Request* r = it->second;
   if (info) {
     info->status = r->status;
@@ -147,15 +409,16 @@ int hweno_poll(hweno_engine* e, uint64_t ticket, double* out, hweno_result* info
     info->t_admit = r->t_admit;
     info->t_finish = r->t_finish;
   }
-  if (r->status == HWENO_OK) {
-    if (out && !r->result.empty()) std::memcpy(out, r->result.data(), sizeof(double) * r->result.size());
-    if (out) {
-      s->all.erase(it);
-      delete r;
-    }
-    return HWENO_OK;
+  const int st = r->status;
+  if (st == HWENO_OK && out) {
+    std::memcpy(out, r->result.data(), sizeof(double) * r->result.size());
+    s->all.erase(it);
+    delete r;
+  } else if (st < 0 && out) {
+    s->all.erase(it);
+    delete r;
   }
-  return r->status;
+  return st;
 }
 
 }  // extern "C"

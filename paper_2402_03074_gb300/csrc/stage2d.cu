@@ -1,426 +1,56 @@
-// stage2d.cu -- fused HWENO-U stage kernel for 2D grids (Sec. 2.2, Eq. 2.16, 2.23, 2.13).
-//
-// Decomposition: a block owns a band of BW-2 output columns and a chunk of output rows
-// [j0, j1).  Its BW threads stand for the columns i0-1 .. i0+BW-2 (the band plus one ring
-// column on each side) and sweep the rows j0-1 .. j1 in order.  At row j every thread
-// reconstructs its cell (i, j) once from a 4-row shared-memory window of the stage input;
-// the x-face fluxes of row j are formed once per face through shared memory, the y-face
-// flux between rows j-1 and j is formed by the column's own thread from the top traces it
-// kept from row j-1, and the cell (i, j-1) is then complete: its stage update is written
-// and the wave speed of the output is folded into a block maximum.  Redundant work is the
-// two ring columns per band and the two ring rows per chunk (x pass skipped on ring rows).
-#include "hweno_device.cuh"
+// stage2d.cu -- single-solve launch of the fused 2D HWENO-U stage (one block per band x
+// row chunk; the work item itself is in stage2d_item.cuh).
 #include "launch.h"
+#include "stage2d_item.cuh"
 
 namespace hw {
 
-// Gauss weights on [-1/2, 1/2] (sum 1) and nodes
-#define GW0 (5.0 / 18.0)
-#define GW1 (4.0 / 9.0)
-
-template <int EQ, typename R>
-__device__ __forceinline__ void flux_dir(const KProblem& P, int dir, const R* u, R* f) {
-  if constexpr (EQ == EQ_EULER) euler_flux<2, R>(P, dir, u, f);
-  else Phys<EQ, R>::flux(P, dir, u, f);
-}
-
-// sum_g sum_h w_g w_h f(u(xi_g, eta_h)) over the 3x3 interior points (index 3g+h)
-template <int EQ, int NC, typename R>
-__device__ __forceinline__ void volume_sum(const KProblem& P, int dir, const R (&in)[9][NC],
-                                           R (&vol)[NC]) {
-  const R wc = R(GW0 * GW0), we = R(GW0 * GW1), wm = R(GW1 * GW1);
-#pragma unroll
-  for (int c = 0; c < NC; ++c) vol[c] = R(0);
-#pragma unroll
-  for (int p = 0; p < 9; ++p) {
-    R f[NC];
-    flux_dir<EQ, R>(P, dir, in[p], f);
-    const int g = p / 3, h = p % 3;
-    const R wgt = (g == 1 && h == 1) ? wm : ((g == 1 || h == 1) ? we : wc);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) vol[c] += wgt * f[c];
-  }
-}
-
+// single-solve kernel: one block per (band, chunk)
 template <int EQ, bool CHAR, typename R, int BW>
-__global__ void __launch_bounds__(BW, 1) stage2d_kernel(KProblem P, KStage S, int rows) {
-  constexpr int NC = (EQ == EQ_EULER) ? 4 : 1;
-  constexpr int NM = 3;
-  constexpr int NA = NC * NM;
-  constexpr int WC = BW + 2;  // window columns: global columns i0-2 .. i0+BW-1
+__global__ void __launch_bounds__(BW, 1) stage2d_kernel(KProblem P, KStage S, int rows, int wout) {
   if (S.active && *S.active == 0) return;
   extern __shared__ double smem[];
-  double* win = smem;                                   // [4 rows][NA][WC]
-  R* trL = reinterpret_cast<R*>(win + 4 * NA * WC);     // [NC][3][2][BW]
-  R* fhx = trL + NC * 3 * 2 * BW;                        // [NC][3][BW]: left face of thread t
   __shared__ double red[2][BW / 32];
+  stage2d_item<EQ, CHAR, R, BW>(P, S, blockIdx.x, blockIdx.y, rows, wout, smem, red);
+}
 
-  const int nx = P.nx, ny = P.ny;
-  const size_t plane = (size_t)nx * ny;
-  const int t = threadIdx.x;
-  const int i0 = blockIdx.x * (BW - 2);
-  const int i = i0 - 1 + t;
-  const int j0 = blockIdx.y * rows;
-  const int j1 = min(ny, j0 + rows);
-  const bool need = (i <= nx);
-  const bool outc = (t >= 1 && t <= BW - 2 && i < nx);
-  const R a1 = (R)S.alpha_in[0], a2 = (R)S.alpha_in[1];
-  const double dt = *S.dt;
-  const R idx = (R)P.inv_dx, idy = (R)P.inv_dy;
-  const R s15 = R(HW_S15);
-
-  auto load_row = [&](int r) {
-    int fy;
-    const int rr = bc_map(r, ny, P.bc[2], P.bc[3], fy);
-    double* dst = win + (r & 3) * NA * WC;
-    for (int q = t; q < NA * WC; q += BW) {
-      const int a = q / WC, col = q - a * WC;
-      int fx;
-      const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], fx);
-      double val = S.Uin[(size_t)a * plane + (size_t)rr * nx + ii];
-      if (fx | fy) val *= mirror_sign<EQ, 2>(a / NM, a % NM, fx, fy);
-      dst[a * WC + col] = val;
-    }
-  };
-#pragma unroll 1
-  for (int r = j0 - 2; r <= j0 + 1; ++r) load_row(r);
-  __syncthreads();
-
-  // state carried from row j-1 to row j
-  R prevT[3][NC], prevTg[3][NC];   // top traces of (i, j-1) and g of them
-  R pend[NC][3];                   // F^1..F^3 of (i, j-1) without its top face
-  R pvh[NC], pwh[NC];              // v-hat, w-hat of (i, j-1)
-  double wmax0 = 0.0, wmax1 = 0.0;
-
-#pragma unroll 1
-  for (int j = j0 - 1; j <= j1; ++j) {
-    const double* wm = win + ((j - 1) & 3) * NA * WC;
-    const double* w0 = win + (j & 3) * NA * WC;
-    const double* wp = win + ((j + 1) & 3) * NA * WC;
-    auto Wv = [&](int a, int k) -> R {   // moment array a of stencil cell k (0..8)
-      const double* rowp = (k < 3) ? wm : (k < 6 ? w0 : wp);
-      return (R)rowp[a * WC + t + (k % 3)];
-    };
-    const bool xrow = (j >= j0 && j < j1);
-
-    R xl[3][NC], xr[3][NC], volf[NC], vh[NC];
-    R yb[3][NC], yt[3][NC], volg[NC], wh[NC];
-    if (need) {
-      if constexpr (CHAR && EQ == EQ_EULER) {
-        R U5[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) U5[c] = Wv(c * NM, 4);
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-          if (pass == 0 && !xrow) continue;
-          Eig2<R> E;
-          E.init(P, pass, U5);
-          R ch[16][4];  // characteristic values: 6 edge points, 9 interior, modification
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            R u[9], v[4], w[4];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-              R Uk[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) Uk[c] = Wv(c * NM, k);
-              u[k] = E.project_field(f, Uk);
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int k = 2 * e + 1;
-              R Vk[4], Zk[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                Vk[c] = Wv(c * NM + 1, k);
-                Zk[c] = Wv(c * NM + 2, k);
-              }
-              v[e] = E.project_field(f, Vk);
-              w[e] = E.project_field(f, Zk);
-            }
-            R C[15];
-            recon2d_coeffs<R>(u, v, w, P, C);
-            R ea[3], eb[3], in[9];
-            if (pass == 0) {
-              eval_xpass(C, ea, eb, in);
-              ch[15][f] = vhat2d(C);
-            } else {
-              eval_ypass(C, ea, eb, in);
-              ch[15][f] = what2d(C);
-            }
-#pragma unroll
-            for (int g = 0; g < 3; ++g) {
-              ch[g][f] = ea[g];
-              ch[3 + g][f] = eb[g];
-            }
-#pragma unroll
-            for (int p = 0; p < 9; ++p) ch[6 + p][f] = in[p];
-          }
-          R cons[16][4];
-#pragma unroll
-          for (int p = 0; p < 16; ++p) E.unproject(ch[p], cons[p]);
-          R inn[9][4];
-#pragma unroll
-          for (int p = 0; p < 9; ++p)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) inn[p][c] = cons[6 + p][c];
-          if (pass == 0) {
-#pragma unroll
-            for (int g = 0; g < 3; ++g)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                xl[g][c] = cons[g][c];
-                xr[g][c] = cons[3 + g][c];
-              }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) vh[c] = cons[15][c];
-            volume_sum<EQ, NC, R>(P, 0, inn, volf);
-          } else {
-#pragma unroll
-            for (int g = 0; g < 3; ++g)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                yb[g][c] = cons[g][c];
-                yt[g][c] = cons[3 + g][c];
-              }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) wh[c] = cons[15][c];
-            volume_sum<EQ, NC, R>(P, 1, inn, volg);
-          }
-        }
-      } else {
-        // component-wise: one reconstruction per conserved component gives all points
-        R inn[9][NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          R u[9], v[4], w[4];
-#pragma unroll
-          for (int k = 0; k < 9; ++k) u[k] = Wv(c * NM, k);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            v[e] = Wv(c * NM + 1, 2 * e + 1);
-            w[e] = Wv(c * NM + 2, 2 * e + 1);
-          }
-          R C[15];
-          recon2d_coeffs<R>(u, v, w, P, C);
-          R ea[3], eb[3], in[9];
-          eval_xpass(C, ea, eb, in);
-#pragma unroll
-          for (int g = 0; g < 3; ++g) {
-            xl[g][c] = ea[g];
-            xr[g][c] = eb[g];
-          }
-#pragma unroll
-          for (int p = 0; p < 9; ++p) inn[p][c] = in[p];
-          R qb[3], qt[3], in2[9];
-          eval_ypass(C, qb, qt, in2);
-#pragma unroll
-          for (int g = 0; g < 3; ++g) {
-            yb[g][c] = qb[g];
-            yt[g][c] = qt[g];
-          }
-          vh[c] = vhat2d(C);
-          wh[c] = what2d(C);
-        }
-        volume_sum<EQ, NC, R>(P, 0, inn, volf);
-        volume_sum<EQ, NC, R>(P, 1, inn, volg);
-      }
-    }
-
-    // y face j-1/2 between (i, j-1) (top traces kept) and (i, j) (bottom traces): Eq. 2.16
-    R ybg[3][NC];
-    if (need) {
-#pragma unroll
-      for (int g = 0; g < 3; ++g) flux_dir<EQ, R>(P, 1, yb[g], ybg[g]);
-    }
-    R rhs[NC][3];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) rhs[c][0] = rhs[c][1] = rhs[c][2] = R(0);
-    if (need && j > j0 - 1) {
-      R gh[3][NC];
-#pragma unroll
-      for (int g = 0; g < 3; ++g)
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-          gh[g][c] = R(0.5) * (prevTg[g][c] + ybg[g][c] - a2 * (yb[g][c] - prevT[g][c]));
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const R sw = R(GW0) * (gh[0][c] + gh[2][c]) + R(GW1) * gh[1][c];
-        const R sm = R(GW0) * s15 * (gh[2][c] - gh[0][c]);
-        // top face of (i, j-1): F1 -= sum/dy, F2 -= sum xi/dy, F3 -= sum/(2 dy)
-        pend[c][0] -= sw * idy;
-        pend[c][1] -= sm * idy;
-        pend[c][2] -= R(0.5) * sw * idy;
-        // bottom face of (i, j): F1 += sum/dy, F2 += sum xi/dy, F3 -= sum/(2 dy)
-        rhs[c][0] = sw * idy;
-        rhs[c][1] = sm * idy;
-        rhs[c][2] = -R(0.5) * sw * idy;
-      }
-      // stage update of (i, j-1): Eq. 2.13
-      if (outc && j - 1 >= j0) {
-        const size_t q = (size_t)(j - 1) * nx + i;
-        double outv[NC * NM];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const double own[3] = {wm[(c * NM) * WC + t + 1], (double)pvh[c], (double)pwh[c]};
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            const size_t qa = (size_t)(c * NM + m) * plane + q;
-            double base;
-            if (S.k == 1) {
-              base = own[m];
-              if (m > 0) S.Vh[(size_t)(c * 2 + m - 1) * plane + q] = own[m];
-            } else {
-              base = (m == 0) ? S.Un[qa] : S.Vh[(size_t)(c * 2 + m - 1) * plane + q];
-            }
-            const double adv = fma(dt, (double)pend[c][m], own[m]);
-            double o;
-            if (S.k == 1) o = adv;
-            else if (S.k == 2) o = fma(0.75, base, 0.25 * adv);
-            else o = fma(1.0 / 3.0, base, 2.0 / 3.0 * adv);
-            S.Uout[qa] = o;
-            outv[c * NM + m] = o;
-          }
-        }
-        double ua[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) ua[c] = outv[c * NM];
-        bool bad = false;
-#pragma unroll
-        for (int q2 = 0; q2 < NC * NM; ++q2) bad |= !isfinite(outv[q2]);
-        if constexpr (EQ == EQ_EULER) {
-          bad |= !euler_physical<2>(P, ua);
-          if (!bad) {
-            wmax0 = fmax(wmax0, euler_speed<2>(P, 0, ua));
-            wmax1 = fmax(wmax1, euler_speed<2>(P, 1, ua));
-          }
-        } else {
-          wmax0 = fmax(wmax0, Phys<EQ, double>::speed(P, 0, ua));
-          wmax1 = fmax(wmax1, Phys<EQ, double>::speed(P, 1, ua));
-        }
-        if (bad) atomicOr(S.status, 1u);
-      }
-    }
-
-    // x faces of row j (output rows only): traces through shared memory, one flux per face
-    if (xrow) {
-      R fl[3][NC], fr[3][NC];
-      if (need) {
-#pragma unroll
-        for (int g = 0; g < 3; ++g) {
-          flux_dir<EQ, R>(P, 0, xl[g], fl[g]);
-          flux_dir<EQ, R>(P, 0, xr[g], fr[g]);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            trL[((c * 3 + g) * 2 + 0) * BW + t] = xl[g][c];
-            trL[((c * 3 + g) * 2 + 1) * BW + t] = fl[g][c];
-          }
-        }
-      }
-      __syncthreads();
-      if (need && t < BW - 1 && i < nx) {
-#pragma unroll
-        for (int g = 0; g < 3; ++g)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            const R uR = trL[((c * 3 + g) * 2 + 0) * BW + t + 1];
-            const R fR = trL[((c * 3 + g) * 2 + 1) * BW + t + 1];
-            fhx[(c * 3 + g) * BW + t + 1] = R(0.5) * (fr[g][c] + fR - a1 * (uR - xr[g][c]));
-          }
-      }
-      __syncthreads();
-      if (outc) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const R L0 = fhx[(c * 3 + 0) * BW + t], L1 = fhx[(c * 3 + 1) * BW + t],
-                  L2 = fhx[(c * 3 + 2) * BW + t];
-          const R R0 = fhx[(c * 3 + 0) * BW + t + 1], R1 = fhx[(c * 3 + 1) * BW + t + 1],
-                  R2 = fhx[(c * 3 + 2) * BW + t + 1];
-          const R sdiff = R(GW0) * ((R0 - L0) + (R2 - L2)) + R(GW1) * (R1 - L1);
-          const R ssum = R(GW0) * ((L0 + R0) + (L2 + R2)) + R(GW1) * (L1 + R1);
-          const R smom = R(GW0) * s15 * ((R2 - L2) - (R0 - L0));
-          rhs[c][0] -= sdiff * idx;
-          rhs[c][1] += (volf[c] - R(0.5) * ssum) * idx;
-          rhs[c][2] += volg[c] * idy - smom * idx;
-        }
-      }
-    }
-
-    // carry row j to the next iteration
-    if (need) {
-#pragma unroll
-      for (int g = 0; g < 3; ++g) {
-        R tg[NC];
-        flux_dir<EQ, R>(P, 1, yt[g], tg);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          prevT[g][c] = yt[g][c];
-          prevTg[g][c] = tg[c];
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        pend[c][0] = rhs[c][0];
-        pend[c][1] = rhs[c][1];
-        pend[c][2] = rhs[c][2];
-        pvh[c] = vh[c];
-        pwh[c] = wh[c];
-      }
-    }
-    __syncthreads();                       // every read of row j-1 is done
-    if (j + 3 <= j1 + 1) load_row(j + 3);  // into the slot of row j-1
-    __syncthreads();
-  }
-
-  // block maxima of the output wave speeds -> one atomic per block and direction
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    wmax0 = fmax(wmax0, __shfl_xor_sync(0xffffffffu, wmax0, o));
-    wmax1 = fmax(wmax1, __shfl_xor_sync(0xffffffffu, wmax1, o));
-  }
-  if ((t & 31) == 0) {
-    red[0][t >> 5] = wmax0;
-    red[1][t >> 5] = wmax1;
-  }
-  __syncthreads();
-  if (t == 0) {
-    double m0 = red[0][0], m1 = red[1][0];
-#pragma unroll
-    for (int w = 1; w < BW / 32; ++w) {
-      m0 = fmax(m0, red[0][w]);
-      m1 = fmax(m1, red[1][w]);
-    }
-    atomic_max_nonneg(&S.alpha_out[0], m0);
-    atomic_max_nonneg(&S.alpha_out[1], m1);
-  }
+// Launch geometry: bands of equal width (<= BW-2 output columns) and row chunks sized so
+// that bands x chunks fills the resident block slots of the GPU once.
+struct Geom2D {
+  int bands, wout, chunks, rows;
+};
+static Geom2D geom2d(int nx, int ny, int bw, int slots) {
+  Geom2D g;
+  g.bands = (nx + (bw - 2) - 1) / (bw - 2);
+  g.wout = (nx + g.bands - 1) / g.bands;
+  int ch = slots / g.bands;
+  if (ch < 1) ch = 1;
+  if (ch > ny) ch = ny;
+  g.rows = (ny + ch - 1) / ch;
+  g.chunks = (ny + g.rows - 1) / g.rows;
+  return g;
 }
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
   constexpr int BW = 128;
-  constexpr int NC = (EQ == EQ_EULER) ? 4 : 1;
-  const size_t smem = sizeof(double) * 4 * NC * 3 * (BW + 2) + sizeof(R) * NC * 3 * 2 * BW +
-                      sizeof(R) * NC * 3 * BW;
+  const size_t smem = smem_bytes2d<EQ, R, BW>();
   auto kern = stage2d_kernel<EQ, CHAR, R, BW>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int slots = 0;  // resident blocks per GPU for this instantiation
+  if (slots == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, BW, smem);
+    if (e != cudaSuccess) return e;
+    slots = (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
   }
-  const int bands = (P.nx + (BW - 2) - 1) / (BW - 2);
-  // rows per chunk: enough blocks for one wave over the SMs, few ring rows
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int chunks = (nsm + bands - 1) / bands;
-  if (chunks < 1) chunks = 1;
-  int rows = (P.ny + chunks - 1) / chunks;
-  if (rows < 1) rows = 1;
-  chunks = (P.ny + rows - 1) / rows;
-  dim3 grid(bands, chunks);
-  kern<<<grid, BW, smem, st>>>(P, S, rows);
+  const Geom2D g = geom2d(P.nx, P.ny, BW, slots);
+  dim3 grid(g.bands, g.chunks);
+  kern<<<grid, BW, smem, st>>>(P, S, g.rows, g.wout);
   return cudaGetLastError();
 }
 

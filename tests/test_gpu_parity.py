@@ -41,14 +41,15 @@ def _check_stage(op, hp, k, seed, tol=TOL):
     dt = 0.3 / (alpha[0] / ((op.x1 - op.x0) / op.nx) + (alpha[1] / ((op.y1 - op.y0) / op.ny) if op.dim == 2 else 0.0))
     ref, vref, ost = O.stage(op, k, Uin, Un, Vh if k > 1 else None, alpha, dt)
     got, vgot, a_out, st = gpu_stage(hp, k, Uin, Un, Vh, alpha, dt)
-    assert st == ost == 0
+    assert st == ost   # both sides flag the same non-physical outputs (random data may)
     e = rel_err(got, ref, Uin)
     assert e <= tol, f"stage {k}: max rel err {e:.3e}"
     if k == 1:
         ev = rel_err(vgot, vref, Uin)
         assert ev <= tol, f"v-hat: {ev:.3e}"
-    aref = O.alpha(op, ref)
-    np.testing.assert_allclose(a_out[: op.dim], aref[: op.dim], rtol=1e-13)
+    if ost == 0:
+        aref = O.alpha(op, ref)
+        np.testing.assert_allclose(a_out[: op.dim], aref[: op.dim], rtol=1e-13)
     return e
 
 
@@ -194,23 +195,30 @@ def test_nonphysical_state_is_reported():
 @pytest.mark.parametrize("dim", [1, 2])
 def test_mixed_precision_stage(dim):
     """FP32 bulk / FP64 weights: stage error against the FP64 oracle within 1e-5 of the
-    component scale.  Bound: FP32 unit roundoff u = 2^-24 = 6e-8; a point value is a sum of
-    stencil values with coefficients whose magnitudes add up to about 30 (Appendix), the
-    projection/unprojection and the Euler flux add a few roundings each, and the flux
-    difference enters the update scaled by dt/dx (< 1): about 160 u = 1e-5."""
+    component scale, on the seeded shock-tube / quadrant-vortex workloads.  Bound: FP32 unit
+    roundoff u = 2^-24 = 6e-8; a point value is a sum of stencil values with coefficients
+    whose magnitudes add up to about 30 (Appendix), the projection/unprojection and the Euler
+    flux add a few roundings each, and the flux difference enters the update scaled by dt/dx
+    (< 1): about 160 u = 1e-5."""
     if dim == 1:
-        op, hp = problems(1, "euler", 300, bc=1, precision=1)
+        w = I.shock_tube_1d(5, n=300)
+        hp = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc,
+                            precision=H.HWENO_MIXED32)
     else:
-        op, hp = problems(2, "euler", 200, 30, bc=1, precision=1)
-    for k in (1, 2, 3):
-        Uin, Un, Vh = _inputs(op, 40 + k)
-        if k == 1:
-            Un = Uin
-        alpha = O.alpha(op, Uin)
-        dx = (op.x1 - op.x0) / op.nx
-        dt = 0.3 * dx / alpha.sum()
-        ref, _, _ = O.stage(op, k, Uin, Un, Vh if k > 1 else None, alpha, dt)
-        got, _, _, st = gpu_stage(hp, k, Uin, Un, Vh, alpha, dt)
-        assert st == 0
-        e = rel_err(got, ref, Uin)
+        w = I.quadrant_vortex_2d(3, 128, window=(0, 40, 128, 30))
+        hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1,
+                            y0=w.y0, y1=w.y1, bc=w.bc, precision=H.HWENO_MIXED32)
+    op = _oracle_of(hp)
+    U = w.U0
+    alpha = O.alpha(op, U)
+    dx = (op.x1 - op.x0) / op.nx
+    dt = 0.3 * dx / alpha.sum()
+    ref1, vh, ost = O.stage(op, 1, U, U, None, alpha, dt)
+    assert ost == 0
+    for k, Uin in ((1, U), (2, ref1), (3, ref1)):
+        a = O.alpha(op, Uin)
+        ref, _, ost = O.stage(op, k, Uin, U, vh if k > 1 else None, a, dt)
+        got, _, _, st = gpu_stage(hp, k, Uin, U, vh, a, dt)
+        assert st == ost == 0
+        e = rel_err(got, ref, U)
         assert e <= 1e-5, f"stage {k}: {e:.3e}"

@@ -1,0 +1,186 @@
+"""Served path (continuous batching) on the GPU: every result equals the same solve run alone
+(bitwise: each cell's reconstruction and each face flux are computed by the same code
+whatever the work decomposition), admission under a memory budget, poll semantics, the
+background serving thread, and a cross-check of a served solve against the FP64 oracle."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2402_03074_gb300 import _binding as H
+from paper_2402_03074_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _prob2d(w, t_end, precision=H.HWENO_FP64):
+    return H.make_problem(dim=2, equation=H.HWENO_EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1,
+                          y0=w.y0, y1=w.y1, bc=w.bc, t_end=t_end, precision=precision)
+
+
+def _solo(p, U0, t_end):
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, p, U0)
+        n = H.hweno_advance(eng, sid, t_end)
+        out, t = H.hweno_get_state(eng, sid, np.empty_like(U0))
+    finally:
+        H.hweno_destroy(eng)
+    return out, t, n
+
+
+def _serve_all(eng, tickets, shapes, max_iters=100000):
+    results = {}
+    for _ in range(max_iters):
+        H.hweno_serve(eng, 8)
+        for tk in list(tickets):
+            out = np.empty(shapes[tk])
+            rc, info = H.hweno_poll(eng, tk, out)
+            if rc == H.HWENO_OK:
+                results[tk] = (out, info)
+                tickets.remove(tk)
+        if not tickets:
+            return results
+    raise AssertionError("served solves did not finish")
+
+
+def test_served_results_equal_solo_runs():
+    reqs = []
+    for seed, n, T, prec in [(0, 64, 0.03, 0), (1, 96, 0.02, 0), (2, 130, 0.025, 1), (3, 40, 0.04, 0),
+                             (4, 200, 0.01, 1)]:
+        w = I.quadrant_vortex_2d(seed, n)
+        reqs.append((w, _prob2d(w, T, prec), T))
+    eng = H.hweno_create()
+    try:
+        tickets, shapes = [], {}
+        for w, p, T in reqs:
+            tk = H.hweno_submit(eng, p, w.U0)
+            tickets.append(tk)
+            shapes[tk] = w.U0.shape
+        order = list(tickets)
+        res = _serve_all(eng, tickets, shapes)
+    finally:
+        H.hweno_destroy(eng)
+    for tk, (w, p, T) in zip(order, reqs):
+        out, info = res[tk]
+        solo, t, n = _solo(p, w.U0, T)
+        assert info.t == T and t == T
+        assert info.steps == n
+        np.testing.assert_array_equal(out, solo)
+        assert info.t_arrive <= info.t_admit <= info.t_finish
+
+
+def test_served_mix_with_late_arrivals():
+    """Requests submitted while others are running join the same launches."""
+    w1 = I.quadrant_vortex_2d(5, 100)
+    w2 = I.quadrant_vortex_2d(6, 64)
+    p1, p2 = _prob2d(w1, 0.03), _prob2d(w2, 0.02)
+    eng = H.hweno_create()
+    try:
+        t1 = H.hweno_submit(eng, p1, w1.U0)
+        H.hweno_serve(eng, 4)
+        H.hweno_serve(eng, 4)
+        t2 = H.hweno_submit(eng, p2, w2.U0)
+        res = _serve_all(eng, [t1, t2], {t1: w1.U0.shape, t2: w2.U0.shape})
+    finally:
+        H.hweno_destroy(eng)
+    np.testing.assert_array_equal(res[t1][0], _solo(p1, w1.U0, 0.03)[0])
+    np.testing.assert_array_equal(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
+    assert res[t2][1].t_admit < res[t1][1].t_finish   # overlapped with the first solve
+
+
+def test_admission_by_memory_budget():
+    w = I.quadrant_vortex_2d(7, 64)
+    p = _prob2d(w, 0.01)
+    per_solve = 64 * 64 * 44 * 8 + 4096
+    eng = H.hweno_create(hbm_budget_bytes=2 * per_solve)     # room for two solves at a time
+    try:
+        tickets = [H.hweno_submit(eng, p, w.U0) for _ in range(5)]
+        shapes = {tk: w.U0.shape for tk in tickets}
+        H.hweno_serve(eng, 1)
+        pending = [H.hweno_poll(eng, tk, None)[1] for tk in tickets]
+        admitted = sum(1 for info in pending if info.t_admit > 0)
+        assert admitted == 2
+        res = _serve_all(eng, list(tickets), shapes)
+    finally:
+        H.hweno_destroy(eng)
+    solo = _solo(p, w.U0, 0.01)[0]
+    for tk in tickets:
+        np.testing.assert_array_equal(res[tk][0], solo)
+
+
+def test_poll_semantics():
+    w = I.quadrant_vortex_2d(8, 32)
+    p = _prob2d(w, 0.01)
+    eng = H.hweno_create()
+    try:
+        with pytest.raises(H.HwenoError) as ei:
+            H.hweno_poll(eng, 12345, None)
+        assert ei.value.code == H.HWENO_ERR_ARG
+        tk = H.hweno_submit(eng, p, w.U0)
+        rc, info = H.hweno_poll(eng, tk, None)
+        assert rc == H.HWENO_PENDING
+        bad = _prob2d(w, 0.0)
+        with pytest.raises(H.HwenoError):
+            H.hweno_submit(eng, bad, w.U0)           # t_end must be > 0
+        res = _serve_all(eng, [tk], {tk: w.U0.shape})
+        with pytest.raises(H.HwenoError):
+            H.hweno_poll(eng, tk, None)              # retired after the result was taken
+    finally:
+        H.hweno_destroy(eng)
+    assert res[tk][1].status == H.HWENO_OK
+
+
+def test_background_server_thread():
+    w = I.quadrant_vortex_2d(9, 48)
+    p = _prob2d(w, 0.02)
+    eng = H.hweno_create(server_thread=1)
+    try:
+        tk = H.hweno_submit(eng, p, w.U0)
+        out = np.empty_like(w.U0)
+        t0 = time.time()
+        while True:
+            rc, info = H.hweno_poll(eng, tk, out)
+            if rc == H.HWENO_OK:
+                break
+            assert time.time() - t0 < 60
+            time.sleep(0.002)
+    finally:
+        H.hweno_destroy(eng)
+    np.testing.assert_array_equal(out, _solo(p, w.U0, 0.02)[0])
+
+
+def test_served_solve_matches_oracle():
+    w = I.quadrant_vortex_2d(10, 24)
+    p = _prob2d(w, 0.02)
+    op = O.Problem(dim=2, eq=O.EULER, nx=24, ny=24, x0=w.x0, x1=w.x1, y0=w.y0, y1=w.y1, bc=w.bc)
+    eng = H.hweno_create()
+    try:
+        tk = H.hweno_submit(eng, p, w.U0)
+        res = _serve_all(eng, [tk], {tk: w.U0.shape})
+    finally:
+        H.hweno_destroy(eng)
+    ref, t, ns, st = O.run(op, w.U0, 0.0, 0.02)
+    out, info = res[tk]
+    assert info.steps == ns
+    S = np.abs(w.U0[:, 0]).max(axis=(1, 2))[:, None, None, None]
+    err = (np.abs(out - ref) / np.maximum(np.abs(ref), S)).max()
+    assert err <= 1e-12 * ns
+
+
+def test_served_1d_and_2d_together():
+    w1 = I.shock_tube_1d(2, n=500, t_end=0.05)
+    p1 = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=w1.nx, x0=w1.x0, x1=w1.x1, bc=w1.bc,
+                        t_end=0.05)
+    w2 = I.quadrant_vortex_2d(11, 64)
+    p2 = _prob2d(w2, 0.02)
+    eng = H.hweno_create()
+    try:
+        t1 = H.hweno_submit(eng, p1, w1.U0)
+        t2 = H.hweno_submit(eng, p2, w2.U0)
+        res = _serve_all(eng, [t1, t2], {t1: w1.U0.shape, t2: w2.U0.shape})
+    finally:
+        H.hweno_destroy(eng)
+    np.testing.assert_array_equal(res[t1][0], _solo(p1, w1.U0, 0.05)[0])
+    np.testing.assert_array_equal(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
