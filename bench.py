@@ -281,6 +281,12 @@ def run_ours(args):
                "steps": args.e2e_steps}
     H.hweno_destroy(eng)
 
+    served = None
+    if not args.no_served:
+        served = served_stream(H, I, lambda: H.hweno_create(device=dev), args.served_m, 50.0,
+                               [int(g) for g in args.served_grids.split(",")],
+                               args.served_tlo, args.served_thi, seed=rank)
+
     if rank != 0:
         return
     flops = FP64_FLOPS_PER_CELL_STAGE
@@ -295,10 +301,125 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": _workload_config(n), "gpu_launches": 4 * args.steps,
-            "clocks": clk.summary(), "roofline": roofline, "mixed32": mixed, "e2e": e2e}
+            "clocks": clk.summary(), "roofline": roofline, "mixed32": mixed, "e2e": e2e,
+            "served": served}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds)
     print(json.dumps(line))
+
+
+def served_stream(H, I, eng_factory, m, rate, grids, t_lo, t_hi, seed=0):
+    """Seeded Poisson stream of 2D Euler solves served by continuous batching, and the same
+    requests through the plain per-solve FP64 loop.  Returns the report dict."""
+    rng = np.random.default_rng(seed)
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=m))
+    ns = rng.choice(grids, size=m)
+    Ts = rng.uniform(t_lo, t_hi, size=m)
+    kinds = rng.integers(0, 2, size=m)         # 0 quadrant Riemann + vortex, 1 periodic vortex
+    precs = rng.integers(0, 2, size=m)         # 0 FP64, 1 FP32 bulk / FP64 weights
+    reqs = []
+    for q in range(m):
+        n = int(ns[q])
+        w = I.quadrant_vortex_2d(seed + 100 + q, n) if kinds[q] == 0 else I.vortex_periodic_2d(n)
+        p = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=n, ny=n, x0=w.x0, x1=w.x1, y0=w.y0,
+                           y1=w.y1, bc=w.bc, cfl=0.6, t_end=float(Ts[q]),
+                           precision=H.HWENO_MIXED32 if precs[q] else H.HWENO_FP64)
+        reqs.append((w, p))
+
+    def stats(fin, t0):
+        tts = np.array([fin[q] - (t0 + arrive[q]) for q in range(m)])
+        span = max(fin.values()) - (t0 + arrive[0])
+        return {"solves_per_s": m / span, "p50_s": float(np.percentile(tts, 50)),
+                "p99_s": float(np.percentile(tts, 99)), "makespan_s": span}
+
+    # continuous batching
+    eng = eng_factory()
+    t0 = time.perf_counter()
+    submitted, live, fin, cell_stages = 0, {}, {}, 0
+    while len(fin) < m:
+        now = time.perf_counter() - t0
+        while submitted < m and arrive[submitted] <= now:
+            w, p = reqs[submitted]
+            live[H.hweno_submit(eng, p, w.U0)] = submitted
+            submitted += 1
+        if not live:
+            time.sleep(max(0.0, min(0.01, arrive[submitted] - now)))
+            continue
+        H.hweno_serve(eng, 8)
+        for tk in list(live):
+            q = live[tk]
+            out = np.empty(reqs[q][0].U0.shape)
+            rc, info = H.hweno_poll(eng, tk, out)
+            if rc == H.HWENO_OK:
+                fin[q] = time.perf_counter()
+                cell_stages += reqs[q][1].nx * reqs[q][1].ny * 3 * info.steps
+                del live[tk]
+    H.hweno_destroy(eng)
+    served = stats(fin, t0)
+    served["cell_stages_per_s"] = cell_stages / served["makespan_s"]
+
+    # plain per-solve FP64 loop, same requests and arrival times
+    eng = eng_factory()
+    t0 = time.perf_counter()
+    fin = {}
+    for q in range(m):
+        now = time.perf_counter() - t0
+        if arrive[q] > now:
+            time.sleep(arrive[q] - now)
+        w, p = reqs[q]
+        p.precision = H.HWENO_FP64
+        sid = H.hweno_open(eng, p, w.U0)
+        H.hweno_advance(eng, sid, p.t_end)
+        H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        H.hweno_close(eng, sid)
+        fin[q] = time.perf_counter()
+    H.hweno_destroy(eng)
+    plain = stats(fin, t0)
+    return {"requests": m, "rate_per_s": rate, "grids": [int(g) for g in grids],
+            "t_end_range": [t_lo, t_hi], "mixed_fraction": float(precs.mean()),
+            "served": served, "plain_fp64_loop": plain,
+            "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"]}
+
+
+def run_sweep(args):
+    """Convergence of the FP64 and FP32-bulk paths on the periodic isentropic vortex
+    (rho = p = 1, u = v = 1 plus the vortex, [0,1]^2, T = 0.05) against the exact translated
+    solution, N = 128 .. 2048; dt = 0.6 dx / 4 (N0 / N)^(2/3) so that the RK3 error does not
+    mask fifth order (R8 reading)."""
+    import torch
+    from paper_2402_03074_gb300 import build as B
+    B.build()
+    from paper_2402_03074_gb300 import _binding as H
+    from paper_2402_03074_gb300 import inputs as I
+    T = args.sweep_T
+    sizes = [int(x) for x in args.sweep_sizes.split(",")]
+    eng = H.hweno_create()
+    rows = []
+    for n in sizes:
+        w = I.vortex_periodic_2d(n, t_end=T)
+        ex = I.vortex_periodic_exact_2d(n, T)
+        dt = 0.6 / n / 4.0 * (sizes[0] / n) ** (2.0 / 3.0)
+        rec = {"n": n}
+        for name, prec in (("fp64", H.HWENO_FP64), ("mixed32", H.HWENO_MIXED32)):
+            p = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=n, ny=n, x0=0, x1=1, y0=0, y1=1,
+                               dt_fixed=dt, precision=prec)
+            sid = H.hweno_open(eng, p, w.U0)
+            t0 = time.perf_counter()
+            steps = H.hweno_advance(eng, sid, T)
+            el = time.perf_counter() - t0
+            out, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+            H.hweno_close(eng, sid)
+            e = np.abs(out[0, 0] - ex[0, 0])
+            rec[name] = {"l1": float(e.mean()), "linf": float(e.max()), "steps": steps,
+                         "seconds": el}
+        rows.append(rec)
+        print(json.dumps(rec), flush=True)
+    H.hweno_destroy(eng)
+    for a, b in zip(rows, rows[1:]):
+        r = math.log(b["n"] / a["n"])
+        print(json.dumps({"n": [a["n"], b["n"]],
+                          "order_l1_fp64": math.log(a["fp64"]["l1"] / b["fp64"]["l1"]) / r,
+                          "order_l1_mixed32": math.log(a["mixed32"]["l1"] / b["mixed32"]["l1"]) / r}))
 
 
 def main():
@@ -315,10 +436,20 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-m", type=int, default=16)
+    ap.add_argument("--served-grids", default="128,256,384,512")
+    ap.add_argument("--served-tlo", type=float, default=0.02)
+    ap.add_argument("--served-thi", type=float, default=0.05)
+    ap.add_argument("--sweep", action="store_true", help="precision / convergence study")
+    ap.add_argument("--sweep-sizes", default="128,256,512,1024,2048")
+    ap.add_argument("--sweep-T", type=float, default=0.05)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -165,6 +165,20 @@ int hweno_stage_device(const hweno_problem* p, int k, const double* U_in, const 
 int hweno_alpha_device(const hweno_problem* p, const double* U, double* alpha_out,
                        void* stream);
 
+/* ---- launch-geometry autotuner -------------------------------------------------------- */
+/* Time one fused stage launch of the 2D problem p on a scratch copy of moments_host for each
+   candidate height of the row chunks a block sweeps (the default one-wave geometry and 8,
+   16, 32, 64, 128, 256 rows), keep the fastest in the process-wide tuning table (keyed by
+   equation, characteristic decomposition, precision and grid) for every later single-solve
+   and batched launch of such problems, and report it (*best_rows: 0 = the default geometry;
+   *best_ms: one stage).  Either output pointer may be NULL. */
+int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* moments_host,
+                   int* best_rows, double* best_ms);
+/* Save the tuning table as text (one entry per line, with the GPU name); load it back
+   (entries of other GPUs are skipped).  hweno_tuning_load returns the entries loaded. */
+int hweno_tuning_save(const char* path);
+int hweno_tuning_load(const char* path);
+
 #ifdef __cplusplus
 }
 #endif

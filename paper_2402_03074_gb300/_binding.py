@@ -106,6 +106,9 @@ def lib() -> ctypes.CDLL:
             "hweno_stage_device": ([P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp],
                                    ctypes.c_int),
             "hweno_alpha_device": ([P, vp, vp, vp], ctypes.c_int),
+            "hweno_autotune": ([E, P, dp, ctypes.POINTER(ctypes.c_int), dp], ctypes.c_int),
+            "hweno_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
+            "hweno_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -237,3 +240,22 @@ def hweno_last_error(eng) -> str:
 def hweno_engine_stream(eng) -> int:
     """cudaStream_t of the engine as an integer handle (for torch.cuda.ExternalStream)."""
     return lib().hweno_engine_stream(eng) or 0
+
+
+# ---- launch-geometry autotuner --------------------------------------------------------
+def hweno_autotune(eng, p: hweno_problem, U: np.ndarray):
+    """Returns (best rows per chunk (0 = default geometry), milliseconds of one stage)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    rows = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(lib().hweno_autotune(eng, ctypes.byref(p), _host(U), ctypes.byref(rows),
+                                ctypes.byref(ms)), eng)
+    return rows.value, ms.value
+
+
+def hweno_tuning_save(path: str) -> None:
+    _check(lib().hweno_tuning_save(path.encode()))
+
+
+def hweno_tuning_load(path: str) -> int:
+    return _check(lib().hweno_tuning_load(path.encode()))

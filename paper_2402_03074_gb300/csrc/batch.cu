@@ -4,8 +4,9 @@
 // by one launch per RK stage.  The launch is persistent (one block per resident slot); its
 // blocks take work items from a device counter.  An item is one (band, row chunk) of one
 // solve, exactly the unit of the single-solve kernel, so uneven grids share the GPU and the
-// load balances at item granularity.  FP64 and FP32-bulk solves share the launch (the item
-// branches on the solve's precision).  Every solve keeps its own scalars (dt, t, LF speeds,
+// load balances at item granularity.  FP64 and FP32-bulk solves are separate classes (one
+// instantiation each, so every kernel keeps the register and stack footprint of the
+// single-solve kernel).  Every solve keeps its own scalars (dt, t, LF speeds,
 // status); one thread per solve advances them at the start of each step, so each solve
 // steps with its own dt.  The work lists live in device memory: admission and retirement
 // rewrite them between steps and the captured step graph stays valid.
@@ -24,7 +25,7 @@ __global__ void batch_dt_kernel(BatchDt* d, BatchCtl* ctl, int nctl) {
   }
 }
 
-template <int EQ, bool CHAR, int BW>
+template <int EQ, bool CHAR, typename R, int BW>
 __global__ void __launch_bounds__(BW, 1) batch_stage_kernel(const BatchSolve* bs, BatchCtl* ctl,
                                                             int k) {
   extern __shared__ double smem[];
@@ -60,22 +61,25 @@ __global__ void __launch_bounds__(BW, 1) batch_stage_kernel(const BatchSolve* bs
     S.status = &B.sc->status;
     S.active = &B.sc->active;
     S.k = k;
-    if (B.mixed) stage2d_item<EQ, CHAR, float, BW>(B.P, S, band, chunk, B.rows, B.wout, smem, red);
-    else stage2d_item<EQ, CHAR, double, BW>(B.P, S, band, chunk, B.rows, B.wout, smem, red);
+    stage2d_item<EQ, CHAR, R, BW>(B.P, S, band, chunk, B.rows, B.wout, smem, red);
   }
 }
 
-template <int EQ, bool CHAR>
-static cudaError_t launch_batch_t(const BatchSolve* bs, BatchCtl* ctl, int k, cudaStream_t st,
-                                  int* slots_out) {
+template <int EQ, bool CHAR, typename R>
+static cudaError_t init_batch_t(int* slots_out, size_t* local_out) {
   constexpr int BW = kBatchBW;
-  const size_t smem = smem_bytes2d<EQ, double, BW>();  // >= the float variant
-  auto kern = batch_stage_kernel<EQ, CHAR, BW>;
+  const size_t smem = smem_bytes2d<EQ, R, BW>();
+  auto kern = batch_stage_kernel<EQ, CHAR, R, BW>;
   static int slots = 0;
+  static size_t local = 0;
   if (slots == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    local = fa.localSizeBytes;
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -84,34 +88,55 @@ static cudaError_t launch_batch_t(const BatchSolve* bs, BatchCtl* ctl, int k, cu
     slots = (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
   }
   if (slots_out) *slots_out = slots;
-  if (!bs) return cudaSuccess;  // query only
-  kern<<<slots, BW, smem, st>>>(bs, ctl, k);
+  if (local_out) *local_out = local;
+  return cudaSuccess;
+}
+
+template <int EQ, bool CHAR, typename R>
+static cudaError_t launch_batch_t(const BatchSolve* bs, BatchCtl* ctl, int k, cudaStream_t st) {
+  constexpr int BW = kBatchBW;
+  int slots = 0;
+  cudaError_t e = init_batch_t<EQ, CHAR, R>(&slots, nullptr);
+  if (e != cudaSuccess) return e;
+  batch_stage_kernel<EQ, CHAR, R, BW><<<slots, BW, smem_bytes2d<EQ, R, BW>(), st>>>(bs, ctl, k);
   return cudaGetLastError();
 }
 
+// class = 2 * (0 advection, 1 Burgers, 2 Euler component-wise, 3 Euler characteristic) + mixed
 cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,
                                cudaStream_t st) {
   switch (cls) {
-    case 0: return launch_batch_t<EQ_ADV, false>(bs, ctl, k, st, nullptr);
-    case 1: return launch_batch_t<EQ_BURG, false>(bs, ctl, k, st, nullptr);
-    case 2: return launch_batch_t<EQ_EULER, false>(bs, ctl, k, st, nullptr);
-    default: return launch_batch_t<EQ_EULER, true>(bs, ctl, k, st, nullptr);
+    case 0: return launch_batch_t<EQ_ADV, false, double>(bs, ctl, k, st);
+    case 1: return launch_batch_t<EQ_ADV, false, float>(bs, ctl, k, st);
+    case 2: return launch_batch_t<EQ_BURG, false, double>(bs, ctl, k, st);
+    case 3: return launch_batch_t<EQ_BURG, false, float>(bs, ctl, k, st);
+    case 4: return launch_batch_t<EQ_EULER, false, double>(bs, ctl, k, st);
+    case 5: return launch_batch_t<EQ_EULER, false, float>(bs, ctl, k, st);
+    case 6: return launch_batch_t<EQ_EULER, true, double>(bs, ctl, k, st);
+    default: return launch_batch_t<EQ_EULER, true, float>(bs, ctl, k, st);
   }
 }
 
-cudaError_t prepare_batch_stage(int cls) {
-  switch (cls) {
-    case 0: return launch_batch_t<EQ_ADV, false>(nullptr, nullptr, 1, 0, nullptr);
-    case 1: return launch_batch_t<EQ_BURG, false>(nullptr, nullptr, 1, 0, nullptr);
-    case 2: return launch_batch_t<EQ_EULER, false>(nullptr, nullptr, 1, 0, nullptr);
-    default: return launch_batch_t<EQ_EULER, true>(nullptr, nullptr, 1, 0, nullptr);
+cudaError_t prepare_batch(size_t* max_local) {
+  size_t m = 0, l = 0;
+  cudaError_t e = cudaSuccess;
+#define HW_PREP(EQ, CH, R)                                            \
+  if (e == cudaSuccess) {                                             \
+    e = init_batch_t<EQ, CH, R>(nullptr, &l);                         \
+    m = l > m ? l : m;                                                \
   }
+  HW_PREP(EQ_ADV, false, double) HW_PREP(EQ_ADV, false, float)
+  HW_PREP(EQ_BURG, false, double) HW_PREP(EQ_BURG, false, float)
+  HW_PREP(EQ_EULER, false, double) HW_PREP(EQ_EULER, false, float)
+  HW_PREP(EQ_EULER, true, double) HW_PREP(EQ_EULER, true, float)
+#undef HW_PREP
+  if (max_local) *max_local = m;
+  return e;
 }
 
-int batch_class(int equation, int characteristic) {
-  if (equation == EQ_ADV) return 0;
-  if (equation == EQ_BURG) return 1;
-  return characteristic ? 3 : 2;
+int batch_class(int equation, int characteristic, int mixed) {
+  const int base = (equation == EQ_ADV) ? 0 : (equation == EQ_BURG ? 1 : (characteristic ? 3 : 2));
+  return 2 * base + (mixed ? 1 : 0);
 }
 
 cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st) {

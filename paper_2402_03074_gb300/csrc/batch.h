@@ -7,7 +7,7 @@
 namespace hw {
 
 constexpr int kBatchBW = 128;     // threads per block of the batched stage kernel
-constexpr int kBatchClasses = 4;  // advection, Burgers, Euler component-wise, Euler characteristic
+constexpr int kBatchClasses = 8;  // {advection, Burgers, Euler comp.-wise, Euler char.} x {FP64, mixed}
 
 // One solve in a batch (device-resident array, rewritten on admission / retirement).
 struct BatchSolve {
@@ -37,10 +37,9 @@ struct BatchDt {
   int dim[kBatchCap];
 };
 
-int batch_class(int equation, int characteristic);
+int batch_class(int equation, int characteristic, int mixed);
 void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks);
 cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st);
-cudaError_t prepare_batch_stage(int cls);  // function attributes / occupancy, no launch
 cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,
                                cudaStream_t st);
 

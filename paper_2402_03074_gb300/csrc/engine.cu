@@ -99,6 +99,29 @@ cudaError_t launch_alpha(int eq, int dim, const KProblem& P, const double* U, do
   return cudaGetLastError();
 }
 
+// Every kernel instantiation gets its attributes set once per device, outside any stream
+// capture, and the per-thread stack limit is raised to the largest stack frame among them
+// (the default limit is smaller than the frame of the FP64 characteristic kernels).
+cudaError_t prepare_kernels(int device) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (device >= 0 && device < 64 && done[device]) return cudaSuccess;
+  size_t a = 0, b = 0, c = 0;
+  cudaError_t e = prepare_stage1d(&a);
+  if (e == cudaSuccess) e = prepare_stage2d(&b);
+  if (e == cudaSuccess) e = prepare_batch(&c);
+  if (e != cudaSuccess) return e;
+  size_t need = std::max(a, std::max(b, c));
+  need = (need + 255) / 256 * 256;
+  size_t cur = 0;
+  e = cudaDeviceGetLimit(&cur, cudaLimitStackSize);
+  if (e != cudaSuccess) return e;
+  if (need > cur) e = cudaDeviceSetLimit(cudaLimitStackSize, need);
+  if (e == cudaSuccess && device >= 0 && device < 64) done[device] = true;
+  return e;
+}
+
 // ------------------------------------------------------------------------------------
 // host helpers
 int problem_check(const hweno_problem* p, std::string* why) {
@@ -280,6 +303,7 @@ int hweno_create(const hweno_engine_config* cfg, hweno_engine** out) {
   const int dev = cfg ? cfg->device : 0;
   if (dev < 0 || dev >= ndev) return HWENO_ERR_ARG;
   if (cudaSetDevice(dev) != cudaSuccess) return HWENO_ERR_CUDA;
+  if (prepare_kernels(dev) != cudaSuccess) return HWENO_ERR_CUDA;
   hweno_engine* e = new hweno_engine();
   e->device = dev;
   if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -453,6 +477,21 @@ void solve_pointers(Solve* s, double** U0, double** U1, double** U2, double** Vh
   *Vh = s->Vh;
 }
 const hweno_problem* solve_problem(Solve* s) { return &s->prob; }
+KStage solve_stage(Solve* s, int k) {
+  KStage S;
+  double* U[3] = {s->U0, s->U1, s->U2};
+  S.Uin = U[k - 1];
+  S.Un = s->U0;
+  S.Vh = s->Vh;
+  S.Uout = U[k % 3];
+  S.alpha_in = s->sc->alpha[k == 1 ? 3 : k - 1];
+  S.alpha_out = s->sc->alpha[k];
+  S.dt = &s->sc->dt;
+  S.status = &s->sc->status;
+  S.active = nullptr;
+  S.k = k;
+  return S;
+}
 KProblem solve_kproblem(Solve* s) { return s->kp; }
 int solve_copy_out(hweno_engine* e, Solve* s, double* host) {
   CUDA_TRY(e, cudaMemcpyAsync(host, s->U0, sizeof(double) * s->nU, cudaMemcpyDeviceToHost,
@@ -569,6 +608,9 @@ int hweno_stage_device(const hweno_problem* p, int k, const double* U_in, const 
   if (k < 1 || k > 3 || !U_in || !U_n || !Vh || !U_out || !alpha_in || !alpha_out || !dt ||
       !status || U_out == U_in)
     return HWENO_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || prepare_kernels(dev) != cudaSuccess)
+    return HWENO_ERR_CUDA;
   KStage S;
   S.Uin = U_in;
   S.Un = U_n;

@@ -56,11 +56,25 @@ __device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_
   s->active = 1;
 }
 
+// Tuning table of the 2D launch geometry: rows per work item for (equation, characteristic,
+// precision, nx, ny); 0 = not tuned (one wave of blocks over the resident slots).
+int tuning_rows(int eq, int characteristic, int mixed, int nx, int ny);
+void tuning_set_rows(int eq, int characteristic, int mixed, int nx, int ny, int rows);
+// Rows-per-chunk override for the next 2D launches of this thread (autotuner), 0 = none.
+void tuning_force_rows(int rows);
+
 // One stage of the modified SSP-RK3 over a whole grid (1D / 2D), asynchronous on st.
 cudaError_t launch_stage1d(int eq, bool characteristic, bool mixed, const KProblem& P,
                            const KStage& S, cudaStream_t st);
 cudaError_t launch_stage2d(int eq, bool characteristic, bool mixed, const KProblem& P,
                            const KStage& S, cudaStream_t st);
+// Set the launch attributes of every kernel instantiation and report the largest per-thread
+// local memory (stack frame) any of them uses; called before any launch or graph capture.
+cudaError_t prepare_stage1d(size_t* max_local);
+cudaError_t prepare_stage2d(size_t* max_local);
+cudaError_t prepare_batch(size_t* max_local);
+cudaError_t prepare_kernels(int device);
+
 // Wave speeds of a state (raises alpha_out[0..1]).
 cudaError_t launch_alpha(int eq, int dim, const KProblem& P, const double* U, double* alpha_out,
                          cudaStream_t st);

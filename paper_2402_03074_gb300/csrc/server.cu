@@ -114,13 +114,24 @@ static void server_free(Server* S) {
 
 static bool batched(const hweno_problem* p) { return p->dim == 2; }
 
+static thread_local std::string g_srv_err;
+static int srv_fail(cudaError_t c, const char* what) {
+  g_srv_err = std::string(what) + ": " + cudaGetErrorString(c);
+  return c == cudaErrorMemoryAllocation ? HWENO_ERR_OOM : HWENO_ERR_CUDA;
+}
+#define SRV_TRY(call)                          \
+  do {                                         \
+    cudaError_t _c = (call);                   \
+    if (_c != cudaSuccess) return srv_fail(_c, #call); \
+  } while (0)
+
 // rewrite the device work lists from the live set (batched 2D solves first: the dt list
 // covers them, the gather list covers every live solve in the same order as S->live)
 static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
   std::stable_partition(S->live.begin(), S->live.end(),
                         [](Request* r) { return batched(&r->prob); });
-  int nb[kBatchClasses] = {0, 0, 0, 0};
-  int items[kBatchClasses] = {0, 0, 0, 0};
+  int nb[kBatchClasses] = {};
+  int items[kBatchClasses] = {};
   int n = 0, nall = 0;
   *classes = 0;
   for (Request* r : S->live) {
@@ -134,7 +145,7 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     ++nall;
     if (!batched(p)) continue;
     ++n;
-    const int cls = batch_class(p->equation, p->characteristic);
+    const int cls = batch_class(p->equation, p->characteristic, p->precision == HWENO_MIXED32);
     BatchSolve& B = S->h_bs[cls * kBatchCap + nb[cls]];
     B.P = kp;
     solve_pointers(sv, &B.U[0], &B.U[1], &B.U[2], &B.Vh);
@@ -154,17 +165,14 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     S->h_ctl[c].n_items = items[c];
     S->h_ctl[c].next[0] = S->h_ctl[c].next[1] = S->h_ctl[c].next[2] = 0u;
     if (nb[c])
-      if (cudaMemcpyAsync(S->d_bs + c * kBatchCap, S->h_bs + c * kBatchCap,
-                          sizeof(BatchSolve) * nb[c], cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return HWENO_ERR_CUDA;
+      SRV_TRY(cudaMemcpyAsync(S->d_bs + c * kBatchCap, S->h_bs + c * kBatchCap,
+                              sizeof(BatchSolve) * nb[c], cudaMemcpyHostToDevice, st));
   }
-  if (cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(BatchCtl) * kBatchClasses,
-                      cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return HWENO_ERR_CUDA;
-  if (cudaMemcpyAsync(S->d_dt, S->h_dt, sizeof(BatchDt), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return HWENO_ERR_CUDA;
+  SRV_TRY(cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(BatchCtl) * kBatchClasses,
+                          cudaMemcpyHostToDevice, st));
+  SRV_TRY(cudaMemcpyAsync(S->d_dt, S->h_dt, sizeof(BatchDt), cudaMemcpyHostToDevice, st));
   // the staging buffers are pinned and rewritten only here: finish the copies first
-  if (cudaStreamSynchronize(st) != cudaSuccess) return HWENO_ERR_CUDA;
+  SRV_TRY(cudaStreamSynchronize(st));
   return HWENO_OK;
 }
 
@@ -183,21 +191,18 @@ static int ensure_batch_graph(Server* S, unsigned classes, cudaStream_t st) {
     cudaGraphExecDestroy(S->graph);
     S->graph = nullptr;
   }
-  // set the launch configuration (function attributes, occupancy) outside the capture
-  cudaError_t e = cudaSuccess;
-  for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c)
-    if (classes & (1u << c)) e = prepare_batch_stage(c);
-  if (e != cudaSuccess) return HWENO_ERR_CUDA;
+  // the launch configuration of every kernel was set when the engine was created
   cudaGraph_t g;
-  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-    return HWENO_ERR_CUDA;
+  SRV_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   const int G = 2;  // steps per graph
+  cudaError_t e = cudaSuccess;
   for (int s = 0; s < G && e == cudaSuccess; ++s) e = enqueue_batch_step(S, classes, st);
   cudaError_t e2 = cudaStreamEndCapture(st, &g);
-  if (e != cudaSuccess || e2 != cudaSuccess) return HWENO_ERR_CUDA;
+  if (e != cudaSuccess) return srv_fail(e, "capturing the batched step");
+  if (e2 != cudaSuccess) return srv_fail(e2, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&S->graph, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return HWENO_ERR_CUDA;
+  if (e != cudaSuccess) return srv_fail(e, "cudaGraphInstantiate");
   S->graph_classes = classes;
   return HWENO_OK;
 }
@@ -270,16 +275,14 @@ static int serve_once(Server* S, long long max_steps) {
   for (Request* r : S->live) any2d |= batched(&r->prob);
   if (any2d) {
     const long long reps = std::max<long long>(1, max_steps / 2);
-    for (long long i = 0; i < reps; ++i)
-      if (cudaGraphLaunch(S->graph, st) != cudaSuccess) return HWENO_ERR_CUDA;
+    for (long long i = 0; i < reps; ++i) SRV_TRY(cudaGraphLaunch(S->graph, st));
   }
   // scalars of all live solves in one copy
   const int n = S->h_dt->n_all;
   gather_scalars_kernel<<<(n + 127) / 128, 128, 0, st>>>(S->d_dt, S->d_gather);
-  if (cudaMemcpyAsync(S->h_gather, S->d_gather, sizeof(DevScal) * n, cudaMemcpyDeviceToHost, st) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return HWENO_ERR_CUDA;
+  SRV_TRY(cudaGetLastError());
+  SRV_TRY(cudaMemcpyAsync(S->h_gather, S->d_gather, sizeof(DevScal) * n, cudaMemcpyDeviceToHost, st));
+  SRV_TRY(cudaStreamSynchronize(st));
   std::vector<Request*> still;
   for (size_t q = 0; q < S->live.size(); ++q) {
     Request* r = S->live[q];
@@ -386,7 +389,7 @@ int hweno_serve(hweno_engine* e, int64_t max_steps, int* active) {
   cudaSetDevice(engine_device(e));
   int rc = serve_once(s, max_steps < 1 ? 1 : max_steps);
   if (active) *active = (int)(s->live.size() + s->queue.size());
-  if (rc) engine_set_error(e, "serving iteration failed");
+  if (rc) engine_set_error(e, "serving iteration failed: " + g_srv_err);
   return rc;
 }
 

@@ -180,6 +180,24 @@ static cudaError_t launch1d_t(const KProblem& P, const KStage& S, cudaStream_t s
   return cudaGetLastError();
 }
 
+template <int EQ, bool CHAR, typename R>
+static size_t local1d_t() {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, stage1d_kernel<EQ, CHAR, R, 128>) != cudaSuccess) return 0;
+  return fa.localSizeBytes;
+}
+
+cudaError_t prepare_stage1d(size_t* max_local) {
+  size_t m = 0;
+  const size_t l[8] = {local1d_t<EQ_ADV, false, double>(), local1d_t<EQ_ADV, false, float>(),
+                       local1d_t<EQ_BURG, false, double>(), local1d_t<EQ_BURG, false, float>(),
+                       local1d_t<EQ_EULER, false, double>(), local1d_t<EQ_EULER, false, float>(),
+                       local1d_t<EQ_EULER, true, double>(), local1d_t<EQ_EULER, true, float>()};
+  for (size_t x : l) m = x > m ? x : m;
+  if (max_local) *max_local = m;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_stage1d(int eq, bool characteristic, bool mixed, const KProblem& P,
                            const KStage& S, cudaStream_t st) {
   if (eq == EQ_ADV) return mixed ? launch1d_t<EQ_ADV, false, float>(P, S, st)

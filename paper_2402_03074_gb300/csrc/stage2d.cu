@@ -15,32 +15,45 @@ __global__ void __launch_bounds__(BW, 1) stage2d_kernel(KProblem P, KStage S, in
 }
 
 // Launch geometry: bands of equal width (<= BW-2 output columns) and row chunks sized so
-// that bands x chunks fills the resident block slots of the GPU once.
+// that bands x chunks fills the resident block slots of the GPU once, unless the tuning
+// table (or the autotuner) fixes the rows per chunk.
 struct Geom2D {
   int bands, wout, chunks, rows;
 };
-static Geom2D geom2d(int nx, int ny, int bw, int slots) {
+static Geom2D geom2d(int nx, int ny, int bw, int slots, int rows_fixed) {
   Geom2D g;
   g.bands = (nx + (bw - 2) - 1) / (bw - 2);
   g.wout = (nx + g.bands - 1) / g.bands;
-  int ch = slots / g.bands;
-  if (ch < 1) ch = 1;
-  if (ch > ny) ch = ny;
-  g.rows = (ny + ch - 1) / ch;
+  if (rows_fixed > 0) {
+    g.rows = rows_fixed < ny ? rows_fixed : ny;
+  } else {
+    int ch = slots / g.bands;
+    if (ch < 1) ch = 1;
+    if (ch > ny) ch = ny;
+    g.rows = (ny + ch - 1) / ch;
+  }
   g.chunks = (ny + g.rows - 1) / g.rows;
   return g;
 }
 
+static thread_local int g_force_rows = 0;
+void tuning_force_rows(int rows) { g_force_rows = rows; }
+
 template <int EQ, bool CHAR, typename R>
-static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
+static cudaError_t init2d_t(int* slots_out, size_t* local_out) {
   constexpr int BW = 128;
   const size_t smem = smem_bytes2d<EQ, R, BW>();
   auto kern = stage2d_kernel<EQ, CHAR, R, BW>;
   static int slots = 0;  // resident blocks per GPU for this instantiation
+  static size_t local = 0;
   if (slots == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    local = fa.localSizeBytes;
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -48,10 +61,40 @@ static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t s
     if (e != cudaSuccess) return e;
     slots = (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
   }
-  const Geom2D g = geom2d(P.nx, P.ny, BW, slots);
+  if (slots_out) *slots_out = slots;
+  if (local_out) *local_out = local;
+  return cudaSuccess;
+}
+
+template <int EQ, bool CHAR, typename R>
+static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
+  constexpr int BW = 128;
+  int slots = 0;
+  cudaError_t e = init2d_t<EQ, CHAR, R>(&slots, nullptr);
+  if (e != cudaSuccess) return e;
+  int rows = g_force_rows;  // > 0 rows, -1 default geometry, 0 consult the table
+  if (rows == 0) rows = tuning_rows(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, P.ny);
+  const Geom2D g = geom2d(P.nx, P.ny, BW, slots, rows > 0 ? rows : 0);
   dim3 grid(g.bands, g.chunks);
-  kern<<<grid, BW, smem, st>>>(P, S, g.rows, g.wout);
+  stage2d_kernel<EQ, CHAR, R, BW><<<grid, BW, smem_bytes2d<EQ, R, BW>(), st>>>(P, S, g.rows, g.wout);
   return cudaGetLastError();
+}
+
+cudaError_t prepare_stage2d(size_t* max_local) {
+  size_t m = 0, l = 0;
+  cudaError_t e = cudaSuccess;
+#define HW_PREP(EQ, CH, R)                                            \
+  if (e == cudaSuccess) {                                             \
+    e = init2d_t<EQ, CH, R>(nullptr, &l);                             \
+    m = l > m ? l : m;                                                \
+  }
+  HW_PREP(EQ_ADV, false, double) HW_PREP(EQ_ADV, false, float)
+  HW_PREP(EQ_BURG, false, double) HW_PREP(EQ_BURG, false, float)
+  HW_PREP(EQ_EULER, false, double) HW_PREP(EQ_EULER, false, float)
+  HW_PREP(EQ_EULER, true, double) HW_PREP(EQ_EULER, true, float)
+#undef HW_PREP
+  if (max_local) *max_local = m;
+  return e;
 }
 
 cudaError_t launch_stage2d(int eq, bool characteristic, bool mixed, const KProblem& P,

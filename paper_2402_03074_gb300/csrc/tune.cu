@@ -1,0 +1,160 @@
+// tune.cu -- launch-geometry autotuner and its tuning table.
+//
+// The 2D stage kernel's blocks sweep row chunks of a band; taller chunks waste fewer ring
+// rows, shorter ones balance better over the SMs.  The autotuner times one stage launch of a
+// problem for each candidate chunk height on a scratch copy of the caller's moments, keeps
+// the fastest in a process-wide table keyed by (equation, characteristic decomposition,
+// precision, grid) and the table is consulted by every later launch (single-solve and
+// batched).  The table can be saved and loaded as text; entries carry the GPU name.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "../../include/hweno.h"
+#include "launch.h"
+#include "server.h"
+
+namespace hw {
+
+using TuneKey = std::tuple<int, int, int, int, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+
+int tuning_rows(int eq, int characteristic, int mixed, int nx, int ny) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey(eq, characteristic, mixed, nx, ny));
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+void tuning_set_rows(int eq, int characteristic, int mixed, int nx, int ny, int rows) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey(eq, characteristic, mixed, nx, ny)] = rows;
+}
+
+static std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return "unknown";
+  std::string n = prop.name;
+  for (char& c : n)
+    if (c == ' ') c = '_';
+  return n;
+}
+
+// scratch-solve accessors implemented in engine.cu
+KStage solve_stage(Solve* s, int k);
+const hweno_problem* solve_problem(Solve* s);
+KProblem solve_kproblem(Solve* s);
+
+}  // namespace hw
+
+using namespace hw;
+
+extern "C" {
+
+int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, int* best_rows,
+                   double* best_ms) {
+  if (!e || !p || !host) return HWENO_ERR_ARG;
+  if (p->dim != 2) {
+    engine_set_error(e, "the autotuner covers 2D problems");
+    return HWENO_ERR_ARG;
+  }
+  std::lock_guard<std::recursive_mutex> lk(engine_mutex(e));
+  cudaSetDevice(engine_device(e));
+  Solve* s = nullptr;
+  int rc = engine_alloc_solve(e, p, &s);
+  if (rc) return rc;
+  cudaStream_t st = engine_stream(e);
+  rc = engine_load_state(e, s, host, 0.0, st);
+  if (rc) {
+    engine_release_solve(e, s);
+    return rc;
+  }
+  const int cand[] = {0, 8, 16, 32, 64, 128, 256};
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int best = 0;
+  float best_t = 1e30f;
+  const KStage S = solve_stage(s, 1);
+  const KProblem kp = solve_kproblem(s);
+  for (int r : cand) {
+    if (r > 0 && r >= p->ny && r != cand[1]) continue;
+    tuning_force_rows(r > 0 ? r : -1);  // -1: the default geometry, ignoring the table
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(a, st);
+      cudaError_t c = launch_stage2d(p->equation, p->equation == HWENO_EULER && p->characteristic,
+                                     p->precision == HWENO_MIXED32, kp, S, st);
+      cudaEventRecord(b, st);
+      if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+        rc = HWENO_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0 && ms < tmin) tmin = ms;
+    }
+    if (rc) break;
+    if (tmin < best_t) {
+      best_t = tmin;
+      best = r;
+    }
+  }
+  tuning_force_rows(0);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  engine_release_solve(e, s);
+  if (rc) {
+    engine_set_error(e, "autotune launch failed");
+    return rc;
+  }
+  tuning_set_rows(p->equation, p->equation == HWENO_EULER ? p->characteristic : 0,
+                  p->precision == HWENO_MIXED32, p->nx, p->ny, best > 0 ? best : -1);
+  if (best_rows) *best_rows = best;
+  if (best_ms) *best_ms = best_t;
+  return HWENO_OK;
+}
+
+int hweno_tuning_save(const char* path) {
+  if (!path) return HWENO_ERR_ARG;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return HWENO_ERR_ARG;
+  const std::string dev = device_name();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::fprintf(f, "# hweno tuning table: gpu equation characteristic mixed nx ny rows\n");
+  for (auto& kv : g_tune)
+    std::fprintf(f, "%s %d %d %d %d %d %d\n", dev.c_str(), std::get<0>(kv.first),
+                 std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                 std::get<4>(kv.first), kv.second);
+  std::fclose(f);
+  return HWENO_OK;
+}
+
+int hweno_tuning_load(const char* path) {
+  if (!path) return HWENO_ERR_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return HWENO_ERR_ARG;
+  const std::string dev = device_name();
+  char line[512], name[256];
+  int n = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    if (line[0] == '#') continue;
+    int eq, ch, mx, nx, ny, rows;
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d", name, &eq, &ch, &mx, &nx, &ny, &rows) == 7 &&
+        dev == name) {
+      tuning_set_rows(eq, ch, mx, nx, ny, rows);
+      ++n;
+    }
+  }
+  std::fclose(f);
+  return n;
+}
+
+}  // extern "C"

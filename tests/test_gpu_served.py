@@ -1,7 +1,14 @@
-"""Served path (continuous batching) on the GPU: every result equals the same solve run alone
-(bitwise: each cell's reconstruction and each face flux are computed by the same code
-whatever the work decomposition), admission under a memory budget, poll semantics, the
-background serving thread, and a cross-check of a served solve against the FP64 oracle."""
+"""Served path (continuous batching) on the GPU.
+
+* A request served in a mix of requests gives bitwise the result of the same request served
+  alone (each cell's reconstruction and each face flux is computed by the same code whatever
+  the work decomposition and whatever else is in the batch).
+* Against the single-solve engine path (hweno_advance; a separate compilation of the same
+  per-item code, so FMA contraction may differ in the last bits): identical step counts and
+  times, FP64 results within 1e-12 of the component scale, FP32-bulk results within 1e-4
+  (FP32 rounding differences, amplified by the nonlinear weights over tens of steps).
+* Admission under a memory budget, poll semantics, the background serving thread, a served
+  solve against the FP64 oracle, and 1D and 2D requests together."""
 import time
 
 import numpy as np
@@ -30,6 +37,15 @@ def _solo(p, U0, t_end):
     return out, t, n
 
 
+def _same(a, b, tol=1e-12, precision=0):
+    if precision == H.HWENO_MIXED32:
+        tol = max(tol, 1e-4)
+    S = np.abs(b[:, 0]).max(axis=(1, 2)).reshape((-1,) + (1,) * (b.ndim - 1))
+    err = float((np.abs(a - b) / np.maximum(np.abs(b), S)).max())
+    assert err <= tol, f"served vs solo: {err:.3e}"
+    return err
+
+
 def _serve_all(eng, tickets, shapes, max_iters=100000):
     results = {}
     for _ in range(max_iters):
@@ -45,12 +61,10 @@ def _serve_all(eng, tickets, shapes, max_iters=100000):
     raise AssertionError("served solves did not finish")
 
 
-def test_served_results_equal_solo_runs():
-    reqs = []
-    for seed, n, T, prec in [(0, 64, 0.03, 0), (1, 96, 0.02, 0), (2, 130, 0.025, 1), (3, 40, 0.04, 0),
-                             (4, 200, 0.01, 1)]:
-        w = I.quadrant_vortex_2d(seed, n)
-        reqs.append((w, _prob2d(w, T, prec), T))
+REQS = [(0, 64, 0.03, 0), (1, 96, 0.02, 0), (2, 130, 0.025, 1), (3, 40, 0.04, 0), (4, 200, 0.01, 1)]
+
+
+def _served(reqs):
     eng = H.hweno_create()
     try:
         tickets, shapes = [], {}
@@ -62,13 +76,33 @@ def test_served_results_equal_solo_runs():
         res = _serve_all(eng, tickets, shapes)
     finally:
         H.hweno_destroy(eng)
-    for tk, (w, p, T) in zip(order, reqs):
-        out, info = res[tk]
+    return [res[tk] for tk in order]
+
+
+def test_served_results_same_alone_and_in_mix():
+    reqs = []
+    for seed, n, T, prec in REQS:
+        w = I.quadrant_vortex_2d(seed, n)
+        reqs.append((w, _prob2d(w, T, prec), T))
+    mix = _served(reqs)
+    for (w, p, T), (out, info) in zip(reqs, mix):
+        alone, ainfo = _served([(w, p, T)])[0]
+        np.testing.assert_array_equal(out, alone)
+        assert info.steps == ainfo.steps and info.t == ainfo.t == T
+        assert info.t_arrive <= info.t_admit <= info.t_finish
+
+
+def test_served_results_match_single_solve_path():
+    reqs = []
+    for seed, n, T, prec in REQS:
+        w = I.quadrant_vortex_2d(seed, n)
+        reqs.append((w, _prob2d(w, T, prec), T))
+    mix = _served(reqs)
+    for (w, p, T), (out, info) in zip(reqs, mix):
         solo, t, n = _solo(p, w.U0, T)
         assert info.t == T and t == T
         assert info.steps == n
-        np.testing.assert_array_equal(out, solo)
-        assert info.t_arrive <= info.t_admit <= info.t_finish
+        _same(out, solo, precision=p.precision)
 
 
 def test_served_mix_with_late_arrivals():
@@ -85,8 +119,8 @@ def test_served_mix_with_late_arrivals():
         res = _serve_all(eng, [t1, t2], {t1: w1.U0.shape, t2: w2.U0.shape})
     finally:
         H.hweno_destroy(eng)
-    np.testing.assert_array_equal(res[t1][0], _solo(p1, w1.U0, 0.03)[0])
-    np.testing.assert_array_equal(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
+    _same(res[t1][0], _solo(p1, w1.U0, 0.03)[0])
+    _same(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
     assert res[t2][1].t_admit < res[t1][1].t_finish   # overlapped with the first solve
 
 
@@ -107,7 +141,7 @@ def test_admission_by_memory_budget():
         H.hweno_destroy(eng)
     solo = _solo(p, w.U0, 0.01)[0]
     for tk in tickets:
-        np.testing.assert_array_equal(res[tk][0], solo)
+        _same(res[tk][0], solo)
 
 
 def test_poll_semantics():
@@ -148,7 +182,7 @@ def test_background_server_thread():
             time.sleep(0.002)
     finally:
         H.hweno_destroy(eng)
-    np.testing.assert_array_equal(out, _solo(p, w.U0, 0.02)[0])
+    _same(out, _solo(p, w.U0, 0.02)[0])
 
 
 def test_served_solve_matches_oracle():
@@ -182,5 +216,5 @@ def test_served_1d_and_2d_together():
         res = _serve_all(eng, [t1, t2], {t1: w1.U0.shape, t2: w2.U0.shape})
     finally:
         H.hweno_destroy(eng)
-    np.testing.assert_array_equal(res[t1][0], _solo(p1, w1.U0, 0.05)[0])
-    np.testing.assert_array_equal(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
+    np.testing.assert_array_equal(res[t1][0], _solo(p1, w1.U0, 0.05)[0])   # same 1D kernel
+    _same(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
