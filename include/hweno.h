@@ -165,6 +165,33 @@ int hweno_stage_device(const hweno_problem* p, int k, const double* U_in, const 
 int hweno_alpha_device(const hweno_problem* p, const double* U, double* alpha_out,
                        void* stream);
 
+/* ---- one batched stage that allocates nothing ---------------------------------------- */
+/* The paper has no counterpart to this entry point: it serves callers that cannot allocate
+   device memory -- applications whose device memory all comes from a pool allocator of
+   their own, and latency-critical loops that cannot afford cudaMalloc / cudaFree, which may
+   synchronise the whole device.  It does what hweno_stage_device does for each of n 2D
+   solves (same equation, characteristic flag and precision), as one persistent launch
+   whose work list and work counter live in a fixed-size static device array of the library
+   (a few KB for at most HWENO_STATIC_BATCH_MAX solves; every GPU that loads the library
+   holds it until the process exits) instead of allocated scratch.  No cudaMalloc, cudaFree
+   or other allocating call is made.  The arrays are host arrays of n entries: problems, and
+   per solve the same device buffers as hweno_stage_device (U_out[s] may alias U_n[s], not
+   U_in[s]).  Every call overwrites the static array, so calls whose work overlaps on the
+   GPU (other streams, other host threads) race on it; calls on one stream are ordered.  The
+   first call on a device sets up that device (looks up the array's device address and the
+   launch configuration), and should come before any stream capture.  Returns
+   HWENO_ERR_ARG for n < 1 or n > HWENO_STATIC_BATCH_MAX, a non-2D or invalid problem, mixed
+   problem classes or a NULL pointer; HWENO_ERR_STATE if the context's per-thread stack limit
+   is below the kernel's stack frame (hweno_create and hweno_stage_device raise it; this
+   entry point does not, because raising it can allocate); HWENO_ERR_CUDA on a launch error.
+   Asynchronous on stream (NULL: the legacy default stream). */
+#define HWENO_STATIC_BATCH_MAX 16
+int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
+                             const double* const* U_in, const double* const* U_n,
+                             double* const* Vh, double* const* U_out,
+                             const double* const* alpha_in, double* const* alpha_out,
+                             const double* const* dt, uint32_t* const* status, void* stream);
+
 /* ---- launch-geometry autotuner -------------------------------------------------------- */
 /* Time one fused stage launch of the 2D problem p on a scratch copy of moments_host for each
    candidate height of the row chunks a block sweeps (the default one-wave geometry and 8,

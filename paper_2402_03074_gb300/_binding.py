@@ -107,6 +107,8 @@ def lib() -> ctypes.CDLL:
                                    ctypes.c_int),
             "hweno_alpha_device": ([P, vp, vp, vp], ctypes.c_int),
             "hweno_autotune": ([E, P, dp, ctypes.POINTER(ctypes.c_int), dp], ctypes.c_int),
+            "hweno_stage_batch_static": ([ctypes.c_int, P, ctypes.c_int, vp, vp, vp, vp, vp, vp,
+                                          vp, vp, vp], ctypes.c_int),
             "hweno_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
             "hweno_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
         }
@@ -259,3 +261,22 @@ def hweno_tuning_save(path: str) -> None:
 
 def hweno_tuning_load(path: str) -> int:
     return _check(lib().hweno_tuning_load(path.encode()))
+
+
+HWENO_STATIC_BATCH_MAX = 16
+
+
+def hweno_stage_batch_static(problems, k, U_in, U_n, Vh, U_out, alpha_in, alpha_out, dt, status,
+                             stream=None) -> None:
+    """One stage of several 2D solves in one launch with no device allocation (static
+    scratch); the lists hold one problem / device buffer per solve."""
+    n = len(problems)
+    arr = (hweno_problem * max(n, 1))(*problems)
+
+    def ptrs(xs):
+        a = (ctypes.c_void_p * max(n, 1))(*[_ptr(x).value if x is not None else None for x in xs])
+        return ctypes.cast(a, ctypes.c_void_p)
+
+    _check(lib().hweno_stage_batch_static(n, arr, k, ptrs(U_in), ptrs(U_n), ptrs(Vh), ptrs(U_out),
+                                          ptrs(alpha_in), ptrs(alpha_out), ptrs(dt), ptrs(status),
+                                          _ptr(stream)))
