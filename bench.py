@@ -36,10 +36,14 @@ UNIT = "cell-stage/s"
 # measured on this machine's GB300 with an FMA-chain probe: 1.19 TFLOP/s FP64, 74 TFLOP/s FP32)
 FP64_PEAK_TFLOPS = 1.19
 FP32_PEAK_TFLOPS = 74.2
-# FP64 flops per cell-stage of the fused 2D Euler characteristic kernel, excluding the ring
-# redundancy: 2 x DFMA + DMUL + DADD thread instructions per launch from ncu on a 256^2 case
-# divided by the cells updated (profiles/stage2d_euler_fp64_2048.md)
-FP64_FLOPS_PER_CELL_STAGE = None
+# FP64 flops per cell-stage of the fused 2D Euler characteristic kernel: 2 x DFMA + DMUL + DADD
+# thread instructions of one 2048^2 launch (ncu) per updated cell, 5920, less the 2.5 % of
+# redundant ring-cell reconstruction (profiles/stage2d_euler_2048_instruction_counts.md)
+FP64_FLOPS_PER_CELL_STAGE = 5776.0
+# DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
+FP64_STAGE_DRAM_BYTES = 428.9e6 + 979.0e6
+# FP64 pipe utilisation of the same kernel from ncu --set full at 1024^2
+FP64_PIPE_UTIL_NCU = 0.851
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
@@ -292,7 +296,9 @@ def run_ours(args):
     flops = FP64_FLOPS_PER_CELL_STAGE
     achieved = flops * n * n / (k_ms / 1e3) / 1e12 if flops else None
     roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                "traffic": FP64_STAGE_DRAM_BYTES if n == 2048 else None,
+                "fp64_pipe_util_ncu": FP64_PIPE_UTIL_NCU,
                 "kernel": "stage2d_kernel<EULER, characteristic, double>",
                 "kernel_ms": k_ms, "flops_per_cell_stage": flops,
                 "hbm_GBps": ALGO_BYTES_PER_CELL_STAGE * n * n / (k_ms / 1e3) / 1e9,

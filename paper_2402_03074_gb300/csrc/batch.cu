@@ -145,6 +145,22 @@ cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaSt
   return cudaGetLastError();
 }
 
+int batch_slots(int cls) {
+  int slots = 0;
+  cudaError_t e;
+  switch (cls) {
+    case 0: e = init_batch_t<EQ_ADV, false, double>(&slots, nullptr); break;
+    case 1: e = init_batch_t<EQ_ADV, false, float>(&slots, nullptr); break;
+    case 2: e = init_batch_t<EQ_BURG, false, double>(&slots, nullptr); break;
+    case 3: e = init_batch_t<EQ_BURG, false, float>(&slots, nullptr); break;
+    case 4: e = init_batch_t<EQ_EULER, false, double>(&slots, nullptr); break;
+    case 5: e = init_batch_t<EQ_EULER, false, float>(&slots, nullptr); break;
+    case 6: e = init_batch_t<EQ_EULER, true, double>(&slots, nullptr); break;
+    default: e = init_batch_t<EQ_EULER, true, float>(&slots, nullptr); break;
+  }
+  return e == cudaSuccess ? slots : 0;
+}
+
 void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks) {
   constexpr int BW = kBatchBW;
   *bands = (nx + (BW - 2) - 1) / (BW - 2);

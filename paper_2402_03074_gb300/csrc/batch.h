@@ -39,6 +39,7 @@ struct BatchDt {
 
 int batch_class(int equation, int characteristic, int mixed);
 void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks);
+int batch_slots(int cls);  // resident blocks of the class's persistent launch
 cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st);
 cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,
                                cudaStream_t st);

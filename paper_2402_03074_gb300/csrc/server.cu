@@ -132,6 +132,24 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
                         [](Request* r) { return batched(&r->prob); });
   int nb[kBatchClasses] = {};
   int items[kBatchClasses] = {};
+  // rows per work item, per class: the items of the class fill its persistent launch's
+  // resident block slots about once (taller items waste fewer ring rows, but a launch with
+  // fewer items than slots leaves SMs idle, e.g. when few solves are left)
+  long long band_rows[kBatchClasses] = {};
+  for (Request* r : S->live) {
+    const hweno_problem* p = solve_problem(r->solve);
+    if (!batched(p)) continue;
+    const int cls = batch_class(p->equation, p->characteristic, p->precision == HWENO_MIXED32);
+    int bands, wout, chunks;
+    batch_geometry(p->nx, p->ny, 1, &bands, &wout, &chunks);
+    band_rows[cls] += (long long)bands * p->ny;
+  }
+  int rows_of[kBatchClasses];
+  for (int c = 0; c < kBatchClasses; ++c) {
+    const int slots = batch_slots(c);
+    long long r = slots > 0 ? band_rows[c] / slots : S->rows;
+    rows_of[c] = (int)(r < 4 ? 4 : (r > 64 ? 64 : r));
+  }
   int n = 0, nall = 0;
   *classes = 0;
   for (Request* r : S->live) {
@@ -151,8 +169,8 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     solve_pointers(sv, &B.U[0], &B.U[1], &B.U[2], &B.Vh);
     B.sc = solve_scalars(sv);
     B.mixed = p->precision == HWENO_MIXED32;
-    B.rows = S->rows;
-    batch_geometry(p->nx, p->ny, S->rows, &B.bands, &B.wout, &B.chunks);
+    B.rows = rows_of[cls];
+    batch_geometry(p->nx, p->ny, B.rows, &B.bands, &B.wout, &B.chunks);
     B.item_base = items[cls];
     items[cls] += B.bands * B.chunks;
     ++nb[cls];
