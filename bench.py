@@ -37,19 +37,37 @@ UNIT = "cell-stage/s"
 FP64_PEAK_TFLOPS = 1.19
 FP32_PEAK_TFLOPS = 74.2
 # FP64 flops per cell-stage of the fused 2D Euler characteristic kernel: 2 x DFMA + DMUL + DADD
-# thread instructions of one 2048^2 launch (ncu) per updated cell, 5920, less the 2.5 % of
+# thread instructions of one 2048^2 launch (ncu) per updated cell, 5911, less the 2.5 % of
 # redundant ring-cell reconstruction (profiles/stage2d_euler_2048_instruction_counts.md)
-FP64_FLOPS_PER_CELL_STAGE = 5776.0
+FP64_FLOPS_PER_CELL_STAGE = 5767.0
 # DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
-FP64_STAGE_DRAM_BYTES = 428.9e6 + 979.0e6
-# FP64 pipe utilisation of the same kernel from ncu --set full at 1024^2
-FP64_PIPE_UTIL_NCU = 0.851
+FP64_STAGE_DRAM_BYTES = 425.5e6 + 757.2e6
+# FP64 pipe utilisation of the same kernel (same capture, % of peak sustained, active cycles)
+FP64_PIPE_UTIL_NCU = 0.857
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
 def _dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's); one
+    all-reduce, on a CUDA tensor under NCCL or a CPU tensor under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Weak scaling over independent replicas: every rank processes units_per_rank units in
+    its own time; the job's throughput is all units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 def _workload_config(n, extra=None):
@@ -214,13 +232,9 @@ def run_ours(args):
     # headline: FP64 path
     with ClockSampler(dev) as clk:
         ms64, out64 = timed_steps(H.HWENO_FP64, args.steps, args.warmup)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms64], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms64 = float(tt.item())
+    ms64 = max_over_ranks(ms64, world, device="cuda")
     cell_stages = n * n * 3 * args.steps
-    value = world * cell_stages / (ms64 / 1e3)
+    value = replica_throughput(cell_stages, ms64, world)
 
     # the fused stage kernel alone: per-launch duration from events on its stream
     p64 = prob(H.HWENO_FP64)

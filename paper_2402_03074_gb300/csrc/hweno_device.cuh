@@ -526,7 +526,7 @@ struct Eig2 {
   int dir;
   __device__ __forceinline__ bool init(const KProblem& P, int d, const R* U) {
     dir = d;
-    const R ir = R(1) / U[0];
+    const R ir = rcp<R>(U[0]);
     const R vx = U[1] * ir, vy = U[2] * ir;
     un = d == 0 ? vx : vy;
     ut = d == 0 ? vy : vx;
@@ -536,11 +536,22 @@ struct Eig2 {
     const R c2 = (R)P.gam * p * ir;
     c = sqrt(c2);
     H = (U[3] + p) * ir;
-    const R b1 = gm1 / c2;
-    b1h = R(0.5) * b1;
+    const R ic2 = rcp<R>(c2);
+    b1h = R(0.5) * gm1 * ic2;
     b2h = q2h * b1h;
-    hic = R(0.5) / c;
+    hic = R(0.5) * rcp<R>(c);
     return p > R(0) && U[0] > R(0);
+  }
+  // W = L U for all four fields (the terms s and t are shared by the acoustic fields)
+  __device__ __forceinline__ void project_all(const R* U, R* W) const {
+    const R mn = dir == 0 ? U[1] : U[2];
+    const R mt = dir == 0 ? U[2] : U[1];
+    const R s = b2h * U[0] - b1h * (un * mn + ut * mt - U[3]);
+    const R t = (un * U[0] - mn) * hic;
+    W[0] = s + t;
+    W[1] = U[0] - R(2) * s;
+    W[2] = mt - ut * U[0];
+    W[3] = s - t;
   }
   // components in the rotated frame: n = normal momentum, t = tangential momentum
   __device__ __forceinline__ R project_field(int f, const R* U) const {

@@ -128,27 +128,37 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           Eig2<R> E;
           E.init(P, pass, U5);
           R ch[16][4];  // characteristic values: 6 edge points, 9 interior, modification
+          // the stencil in characteristic variables, all four fields at once: 9 averages and
+          // the x / y first moments of cells 2, 4, 6, 8
+          R Wu[9][4], Wv_[4][4], Ww[4][4];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            R Uk[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Uk[c] = Wv(c * NM, k);
+            E.project_all(Uk, Wu[k]);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 2 * e + 1;
+            R Vk[4], Zk[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              Vk[c] = Wv(c * NM + 1, k);
+              Zk[c] = Wv(c * NM + 2, k);
+            }
+            E.project_all(Vk, Wv_[e]);
+            E.project_all(Zk, Ww[e]);
+          }
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
             R u[9], v[4], w[4];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-              R Uk[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) Uk[c] = Wv(c * NM, k);
-              u[k] = E.project_field(f, Uk);
-            }
+            for (int k = 0; k < 9; ++k) u[k] = Wu[k][f];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const int k = 2 * e + 1;
-              R Vk[4], Zk[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                Vk[c] = Wv(c * NM + 1, k);
-                Zk[c] = Wv(c * NM + 2, k);
-              }
-              v[e] = E.project_field(f, Vk);
-              w[e] = E.project_field(f, Zk);
+              v[e] = Wv_[e][f];
+              w[e] = Ww[e][f];
             }
             R C[15];
             recon2d_coeffs<R>(u, v, w, P, C);

@@ -233,3 +233,22 @@ def test_stage_cells_equals_full_stage():
                 np.testing.assert_array_equal(out[s], full[:, :, j, i])
                 if k == 1:
                     np.testing.assert_array_equal(vho[s], vh[:, :, j, i])
+
+
+def test_lax_problem_scale_invariance_of_the_weights():
+    """Example 3.5 scaled by zeta = 2^20 (density and pressure): the solution should scale by
+    zeta (Sec. 2.1 Step 3 claims identical weights for u and zeta*u).  Scale-invariant
+    weights: within 4e-3 (epsilon = 1e-10 is absolute); original weights: >= 10x worse."""
+    dev = {}
+    for wm in (O.W_SCALE_INVARIANT, O.W_ORIGINAL):
+        res = {}
+        for zeta in (1.0, 2.0 ** 20):
+            w = I.lax_1d(200, zeta=zeta)
+            P = O.Problem(dim=1, eq=O.EULER, nx=200, x0=-0.5, x1=0.5,
+                          bc=(O.BC_TRANSMISSIVE,) * 4, weights=wm)
+            U, t, ns, st = O.run(P, w.U0, 0.0, 0.16)
+            assert st == 0 and t == 0.16
+            res[zeta] = U[0, 0, 0] / zeta
+        dev[wm] = np.abs(res[2.0 ** 20] - res[1.0]).max() / np.abs(res[1.0]).max()
+    assert dev[O.W_SCALE_INVARIANT] < 4e-3
+    assert dev[O.W_ORIGINAL] > 10 * dev[O.W_SCALE_INVARIANT]
