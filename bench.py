@@ -37,13 +37,13 @@ UNIT = "cell-stage/s"
 FP64_PEAK_TFLOPS = 1.19
 FP32_PEAK_TFLOPS = 74.2
 # FP64 flops per cell-stage of the fused 2D Euler characteristic kernel: 2 x DFMA + DMUL + DADD
-# thread instructions of one 2048^2 launch (ncu) per updated cell, 5911, less the 2.5 % of
+# thread instructions of one 2048^2 launch (ncu) per updated cell, 5667, less the 2.5 % of
 # redundant ring-cell reconstruction (profiles/stage2d_euler_2048_instruction_counts.md)
-FP64_FLOPS_PER_CELL_STAGE = 5767.0
+FP64_FLOPS_PER_CELL_STAGE = 5529.0
 # DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
-FP64_STAGE_DRAM_BYTES = 425.5e6 + 757.2e6
+FP64_STAGE_DRAM_BYTES = 425.9e6 + 673.2e6
 # FP64 pipe utilisation of the same kernel (same capture, % of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.857
+FP64_PIPE_UTIL_NCU = 0.856
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 

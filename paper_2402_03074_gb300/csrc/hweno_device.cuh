@@ -73,15 +73,37 @@ __device__ __forceinline__ double mirror_sign(int c, int m, int fx, int fy) {
   return s;
 }
 
+// Reciprocal 1/x: Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
+// seeded with the single-precision reciprocal of x; two steps take the 2^-22 relative error
+// of the seed below 2^-52 (result within 1 ulp of 1/x).  Values whose exponent is outside
+// +-100 of 1 (where the float seed could over- or underflow) use the division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const long long eb = (__double_as_longlong(x) >> 52) & 0x7ff;
+  if (eb < 1023 - 100 || eb > 1023 + 100) return 1.0 / x;
+  double y = (double)__frcp_rn((float)x);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+template <typename R>
+__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
+template <>
+__device__ __forceinline__ double rcp<double>(double x) { return rcp_nr(x); }
+
 // ---------------------------------------------------------------------------------------
-// nonlinear weights (Eq. 2.10-2.11 / 2.21-2.22), double precision.
-// w~_m = gamma_m (1 + tau/d_m) with d_m = beta_m u_ave + eps > 0; the normalised weights are
-// formed with a single reciprocal: omega_m = gamma_m (D + tau D_m) / sum_k gamma_k (D + tau D_k)
-// with D = prod_k d_k and D_m = prod_{k != m} d_k (equal to the direct formula in exact
-// arithmetic).  If the products leave the normal double range the direct formula is used.
+// nonlinear weights (Eq. 2.10-2.11 / 2.21-2.22), double precision, returned in the form the
+// combined polynomial u = a0 p_0 + sum_{m>0} b_m p_m needs: a0 = omega_0 / gamma_0 and
+// b_m = omega_m - a0 gamma_m.
+// w~_m = gamma_m (1 + tau/d_m) with d_m = beta_m u_ave + eps > 0.  With D = prod_k d_k and
+// D_m = prod_{k != m} d_k, omega_m = gamma_m (D + tau D_m) / S, S = sum_k gamma_k (D + tau D_k)
+// (equal to the direct formula in exact arithmetic), so a0 = (D + tau D_0) / S and
+// b_m = gamma_m tau (D_m - D_0) / S: one reciprocal, and no cancellation beyond that of
+// D_m - D_0.  If the products leave the normal double range the direct formula is used.
 template <int NS>
 __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], double uave,
-                                                  const KProblem& P, double (&om)[NS]) {
+                                                  const KProblem& P, double& a0,
+                                                  double (&b)[NS]) {
   double s = 0.0;
 #pragma unroll
   for (int m = 1; m < NS; ++m) s += fabs(beta[0] - beta[m]);
@@ -101,21 +123,24 @@ __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], doub
 #pragma unroll
   for (int m = NS - 1; m >= 0; --m) suf[m] = (m == NS - 1) ? d[NS - 1] : suf[m + 1] * d[m];
   const double D = pre[NS];
-  double N[NS];
-  double sum = 0.0;
+  double Dm[NS];
 #pragma unroll
-  for (int m = 0; m < NS; ++m) {
-    const double Dm = (m == 0) ? suf[1] : ((m == NS - 1) ? pre[NS - 1] : pre[m] * suf[m + 1]);
-    N[m] = ((m == 0) ? g0 : P.glo) * fma(tau, Dm, D);
-    sum += N[m];
-  }
-  // exponent checks on the INT pipe: D and the sum must be normal and far from overflow
+  for (int m = 0; m < NS; ++m)
+    Dm[m] = (m == 0) ? suf[1] : ((m == NS - 1) ? pre[NS - 1] : pre[m] * suf[m + 1]);
+  const double N0 = fma(tau, Dm[0], D);
+  double nsum = 0.0;
+#pragma unroll
+  for (int m = 1; m < NS; ++m) nsum += fma(tau, Dm[m], D);
+  const double S = fma(g0, N0, P.glo * nsum);
+  // exponent checks on the INT pipe: D and S must be normal and far from overflow
   const long long eD = (__double_as_longlong(D) >> 52) & 0x7ff;
-  const long long eS = (__double_as_longlong(sum) >> 52) & 0x7ff;
+  const long long eS = (__double_as_longlong(S) >> 52) & 0x7ff;
   if (eD > 64 && eD < 2047 - 64 && eS > 64 && eS < 2047 - 64) {
-    const double inv = 1.0 / sum;
+    const double inv = rcp_nr(S);
+    a0 = N0 * inv;
+    const double k = (tau * P.glo) * inv;
 #pragma unroll
-    for (int m = 0; m < NS; ++m) om[m] = N[m] * inv;
+    for (int m = 1; m < NS; ++m) b[m] = k * (Dm[m] - Dm[0]);
   } else {
     double wt[NS];
     double ws = 0.0;
@@ -126,28 +151,12 @@ __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], doub
       ws += wt[m];
     }
     const double inv = 1.0 / ws;
+    a0 = (wt[0] * inv) / g0;
 #pragma unroll
-    for (int m = 0; m < NS; ++m) om[m] = wt[m] * inv;
+    for (int m = 1; m < NS; ++m) b[m] = wt[m] * inv - a0 * P.glo;
   }
+  b[0] = 0.0;
 }
-
-// Reciprocal 1/x: Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
-// seeded with the single-precision reciprocal of x; two steps take the 2^-22 relative error
-// of the seed below 2^-52 (result within 1 ulp of 1/x).  Values whose exponent is outside
-// +-100 of 1 (where the float seed could over- or underflow) use the division.
-__device__ __forceinline__ double rcp_nr(double x) {
-  const long long eb = (__double_as_longlong(x) >> 52) & 0x7ff;
-  if (eb < 1023 - 100 || eb > 1023 + 100) return 1.0 / x;
-  double y = (double)__frcp_rn((float)x);
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
-template <typename R>
-__device__ __forceinline__ R rcp(R x) { return R(1) / x; }
-template <>
-__device__ __forceinline__ double rcp<double>(double x) { return rcp_nr(x); }
 
 // ---------------------------------------------------------------------------------------
 // 1D reconstruction of one field (Sec. 2.1 Steps 1-3, Eq. 2.12).
@@ -182,13 +191,11 @@ __device__ __forceinline__ void recon1d(R um, R u0, R up, R vm, R vp, const KPro
   }
   // Step 3
   const double a = ((double)fabs(um) + (double)fabs(u0) + (double)fabs(up)) * (1.0 / 3.0);
-  double om[3];
-  nonlinear_weights<3>(beta, a * a, P, om);
   // combined polynomial u_i = a0 p_0 + sum_m (omega_m - a0 gamma_m) p_m, a0 = omega_0/gamma_0
-  const double g0 = 1.0 - 2.0 * P.glo;
-  const double a0d = om[0] / g0;
+  double a0d, bm[3];
+  nonlinear_weights<3>(beta, a * a, P, a0d, bm);
   const R a0 = (R)a0d;
-  const R b1 = (R)(om[1] - a0d * P.glo), b2 = (R)(om[2] - a0d * P.glo);
+  const R b1 = (R)bm[1], b2 = (R)bm[2];
   const R C0 = a0 * c0 + (R)(1.0 - a0d) * u0;
   const R C1 = a0 * c1 + b1 * l1 + b2 * l2;
   const R C2 = a0 * c2, C3 = a0 * c3, C4 = a0 * c4;
@@ -305,13 +312,10 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
   // Step 3
   const double a = ((double)fabs(u2) + (double)fabs(u4) + (double)fabs(u5) + (double)fabs(u6) +
                     (double)fabs(u8)) * 0.2;
-  double om[5];
-  nonlinear_weights<5>(beta, a * a, P, om);
-  const double g0 = 1.0 - 4.0 * P.glo;
-  const double a0d = om[0] / g0;
+  double a0d, bm[5];
+  nonlinear_weights<5>(beta, a * a, P, a0d, bm);
   const R a0 = (R)a0d;
-  const R b1 = (R)(om[1] - a0d * P.glo), b2 = (R)(om[2] - a0d * P.glo),
-          b3 = (R)(om[3] - a0d * P.glo), b4 = (R)(om[4] - a0d * P.glo);
+  const R b1 = (R)bm[1], b2 = (R)bm[2], b3 = (R)bm[3], b4 = (R)bm[4];
   C[0] = a0 * c[0] + (R)(1.0 - a0d) * u5;
   C[1] = a0 * c[1] + (b1 + b3) * dl + (b2 + b4) * dr;
   C[2] = a0 * c[2] + (b1 + b2) * db + (b3 + b4) * dtp;
@@ -476,6 +480,22 @@ __device__ __forceinline__ bool euler_physical(const KProblem& P, const double* 
   return e > 0.0 && isfinite(e);
 }
 
+// Admissibility of an output average (rho > 0, internal energy > 0 and finite) and its wave
+// speeds |u| + c, |v| + c in one pass: one reciprocal of rho and one square root.
+template <int DIM>
+__device__ __forceinline__ bool euler_speeds(const KProblem& P, const double* u, double& s0,
+                                             double& s1) {
+  const double ir = rcp_nr(u[0]);
+  const double vx = u[1] * ir;
+  const double vy = DIM == 2 ? u[2] * ir : 0.0;
+  const double e = u[DIM + 1] - 0.5 * (DIM == 2 ? fma(u[1], vx, u[2] * vy) : u[1] * vx);
+  const bool ok = u[0] > 0.0 && e > 0.0 && isfinite(e);
+  const double c = sqrt(P.gam * ((P.gam - 1.0) * e) * ir);
+  s0 = fabs(vx) + c;
+  s1 = fabs(vy) + c;
+  return ok;
+}
+
 // Characteristic decomposition of the Euler equations (Remark 2.2): eigenvectors of the
 // flux Jacobian at a state.  1D columns: u-c, u, u+c.  2D x: u-c, u, shear, u+c (the y
 // Jacobian exchanges the roles of the velocity components).
@@ -534,12 +554,12 @@ struct Eig2 {
     q2h = R(0.5) * (vx * vx + vy * vy);
     const R p = gm1 * (U[3] - U[0] * q2h);
     const R c2 = (R)P.gam * p * ir;
-    c = sqrt(c2);
+    const R rc = rsqrt(c2);       // 1/c; c and 1/c^2 follow from it
+    c = c2 * rc;
     H = (U[3] + p) * ir;
-    const R ic2 = rcp<R>(c2);
-    b1h = R(0.5) * gm1 * ic2;
+    b1h = R(0.5) * gm1 * (rc * rc);
     b2h = q2h * b1h;
-    hic = R(0.5) * rcp<R>(c);
+    hic = R(0.5) * rc;
     return p > R(0) && U[0] > R(0);
   }
   // W = L U for all four fields (the terms s and t are shared by the acoustic fields)

@@ -117,14 +117,66 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
 
     R xl[3][NC], xr[3][NC], volf[NC], vh[NC];
     R yb[3][NC], yt[3][NC], volg[NC], wh[NC];
-    if (need) {
-      if constexpr (CHAR && EQ == EQ_EULER) {
-        R U5[4];
+    R rx[NC][3];                     // x-face and f-volume part of the RHS of (i, j)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) U5[c] = Wv(c * NM, 4);
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-          if (pass == 0 && !xrow) continue;
+    for (int c = 0; c < NC; ++c) rx[c][0] = rx[c][1] = rx[c][2] = R(0);
+
+    // x faces of row j (output rows only): traces through shared memory, one flux per face;
+    // called by every thread of the block (it synchronises)
+    auto xfaces = [&]() {
+      R fl[3][NC], fr[3][NC];
+      if (need) {
+#pragma unroll
+        for (int g = 0; g < 3; ++g) {
+          flux_dir<EQ, R>(P, 0, xl[g], fl[g]);
+          flux_dir<EQ, R>(P, 0, xr[g], fr[g]);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            trL[((c * 3 + g) * 2 + 0) * BW + t] = xl[g][c];
+            trL[((c * 3 + g) * 2 + 1) * BW + t] = fl[g][c];
+          }
+        }
+      }
+      __syncthreads();
+      if (need && t <= wout && i < nx) {
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const R uR = trL[((c * 3 + g) * 2 + 0) * BW + t + 1];
+            const R fR = trL[((c * 3 + g) * 2 + 1) * BW + t + 1];
+            fhx[(c * 3 + g) * BW + t + 1] = R(0.5) * (fr[g][c] + fR - a1 * (uR - xr[g][c]));
+          }
+      }
+      __syncthreads();
+      if (outc) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const R L0 = fhx[(c * 3 + 0) * BW + t], L1 = fhx[(c * 3 + 1) * BW + t],
+                  L2 = fhx[(c * 3 + 2) * BW + t];
+          const R R0 = fhx[(c * 3 + 0) * BW + t + 1], R1 = fhx[(c * 3 + 1) * BW + t + 1],
+                  R2 = fhx[(c * 3 + 2) * BW + t + 1];
+          const R sdiff = R(GW0) * ((R0 - L0) + (R2 - L2)) + R(GW1) * (R1 - L1);
+          const R ssum = R(GW0) * ((L0 + R0) + (L2 + R2)) + R(GW1) * (L1 + R1);
+          const R smom = R(GW0) * s15 * ((R2 - L2) - (R0 - L0));
+          rx[c][0] = -sdiff * idx;
+          rx[c][1] = (volf[c] - R(0.5) * ssum) * idx;
+          rx[c][2] = -smom * idx;
+        }
+      }
+    };
+
+    if constexpr (CHAR && EQ == EQ_EULER) {
+      // two characteristic passes (x: edge points of the x faces, f-volume, v-hat; y: edge
+      // points of the y faces, g-volume, w-hat); the x faces are formed between them so the
+      // x-pass results are dead during the y pass
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 0 && !xrow) continue;
+        if (need) {
+          R U5[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) U5[c] = Wv(c * NM, 4);
           Eig2<R> E;
           E.init(P, pass, U5);
           R ch[16][4];  // characteristic values: 6 edge points, 9 interior, modification
@@ -210,7 +262,10 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
             volume_sum<EQ, NC, R>(P, 1, inn, volg);
           }
         }
-      } else {
+        if (pass == 0) xfaces();
+      }
+    } else {
+      if (need) {
         // component-wise: one reconstruction per conserved component gives all points
         R inn[9][NC];
 #pragma unroll
@@ -247,6 +302,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
         volume_sum<EQ, NC, R>(P, 0, inn, volf);
         volume_sum<EQ, NC, R>(P, 1, inn, volg);
       }
+      if (xrow) xfaces();
     }
 
     // y face j-1/2 between (i, j-1) (top traces kept) and (i, j) (bottom traces): Eq. 2.16
@@ -311,10 +367,11 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
 #pragma unroll
         for (int q2 = 0; q2 < NC * NM; ++q2) bad |= !isfinite(outv[q2]);
         if constexpr (EQ == EQ_EULER) {
-          bad |= !euler_physical<2>(P, ua);
+          double s0, s1;
+          bad |= !euler_speeds<2>(P, ua, s0, s1);
           if (!bad) {
-            wmax0 = fmax(wmax0, euler_speed<2>(P, 0, ua));
-            wmax1 = fmax(wmax1, euler_speed<2>(P, 1, ua));
+            wmax0 = fmax(wmax0, s0);
+            wmax1 = fmax(wmax1, s1);
           }
         } else {
           wmax0 = fmax(wmax0, Phys<EQ, double>::speed(P, 0, ua));
@@ -324,47 +381,13 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
       }
     }
 
-    // x faces of row j (output rows only): traces through shared memory, one flux per face
-    if (xrow) {
-      R fl[3][NC], fr[3][NC];
-      if (need) {
+    // the x-face and volume terms of (i, j)
+    if (xrow && outc) {
 #pragma unroll
-        for (int g = 0; g < 3; ++g) {
-          flux_dir<EQ, R>(P, 0, xl[g], fl[g]);
-          flux_dir<EQ, R>(P, 0, xr[g], fr[g]);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            trL[((c * 3 + g) * 2 + 0) * BW + t] = xl[g][c];
-            trL[((c * 3 + g) * 2 + 1) * BW + t] = fl[g][c];
-          }
-        }
-      }
-      __syncthreads();
-      if (need && t <= wout && i < nx) {
-#pragma unroll
-        for (int g = 0; g < 3; ++g)
-#pragma unroll
-          for (int c = 0; c < NC; ++c) {
-            const R uR = trL[((c * 3 + g) * 2 + 0) * BW + t + 1];
-            const R fR = trL[((c * 3 + g) * 2 + 1) * BW + t + 1];
-            fhx[(c * 3 + g) * BW + t + 1] = R(0.5) * (fr[g][c] + fR - a1 * (uR - xr[g][c]));
-          }
-      }
-      __syncthreads();
-      if (outc) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const R L0 = fhx[(c * 3 + 0) * BW + t], L1 = fhx[(c * 3 + 1) * BW + t],
-                  L2 = fhx[(c * 3 + 2) * BW + t];
-          const R R0 = fhx[(c * 3 + 0) * BW + t + 1], R1 = fhx[(c * 3 + 1) * BW + t + 1],
-                  R2 = fhx[(c * 3 + 2) * BW + t + 1];
-          const R sdiff = R(GW0) * ((R0 - L0) + (R2 - L2)) + R(GW1) * (R1 - L1);
-          const R ssum = R(GW0) * ((L0 + R0) + (L2 + R2)) + R(GW1) * (L1 + R1);
-          const R smom = R(GW0) * s15 * ((R2 - L2) - (R0 - L0));
-          rhs[c][0] -= sdiff * idx;
-          rhs[c][1] += (volf[c] - R(0.5) * ssum) * idx;
-          rhs[c][2] += volg[c] * idy - smom * idx;
-        }
+      for (int c = 0; c < NC; ++c) {
+        rhs[c][0] += rx[c][0];
+        rhs[c][1] += rx[c][1];
+        rhs[c][2] += volg[c] * idy + rx[c][2];
       }
     }
 
