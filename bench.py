@@ -304,6 +304,10 @@ def run_ours(args):
         served = served_stream(H, I, lambda: H.hweno_create(device=dev), args.served_m, 50.0,
                                [int(g) for g in args.served_grids.split(",")],
                                args.served_tlo, args.served_thi, seed=rank)
+    tubes = None
+    if not args.no_tubes:
+        tubes = tubes_1d(H, I, lambda: H.hweno_create(device=dev), args.tubes, args.tubes_n,
+                         args.tubes_t)
 
     if rank != 0:
         return
@@ -322,7 +326,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": _workload_config(n), "gpu_launches": 4 * args.steps,
             "clocks": clk.summary(), "roofline": roofline, "mixed32": mixed, "e2e": e2e,
-            "served": served}
+            "served": served, "tubes_1d": tubes}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds)
     print(json.dumps(line))
@@ -401,6 +405,56 @@ def served_stream(H, I, eng_factory, m, rate, grids, t_lo, t_hi, seed=0):
             "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"]}
 
 
+def tubes_1d(H, I, eng_factory, tubes, n, t_end):
+    """1D Euler shock tubes (seeds 0..tubes-1, n cells, to t_end): every tube through the plain
+    per-solve FP64 loop (one graph-replayed step sequence per tube, one after the other), and
+    all tubes at once through the served path (one persistent launch per stage over the
+    blocks of every tube).  Returns the report dict."""
+    ws = [I.shock_tube_1d(sd, n=n, t_end=t_end) for sd in range(tubes)]
+    probs = [H.make_problem(dim=1, equation=H.HWENO_EULER, nx=n, x0=w.x0, x1=w.x1, bc=w.bc,
+                            cfl=0.6, t_end=t_end) for w in ws]
+    eng = eng_factory()
+    plain_out, steps = [], 0
+    t0 = time.perf_counter()
+    for w, p in zip(ws, probs):
+        sid = H.hweno_open(eng, p, w.U0)
+        steps += H.hweno_advance(eng, sid, t_end)
+        out, _ = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        H.hweno_close(eng, sid)
+        plain_out.append(out)
+    el_plain = time.perf_counter() - t0
+    H.hweno_destroy(eng)
+    eng = eng_factory()
+    t0 = time.perf_counter()
+    tks = [H.hweno_submit(eng, p, w.U0) for w, p in zip(ws, probs)]
+    done, served_out, steps_b = {}, {}, 0
+    while len(done) < len(tks):
+        H.hweno_serve(eng, 64)
+        for q, tk in enumerate(tks):
+            if q in done:
+                continue
+            out = np.empty_like(ws[q].U0)
+            rc, info = H.hweno_poll(eng, tk, out)
+            if rc == H.HWENO_OK:
+                done[q] = info.steps
+                served_out[q] = out
+    el_b = time.perf_counter() - t0
+    H.hweno_destroy(eng)
+    steps_b = sum(done.values())
+    diff = 0.0
+    for q, w in enumerate(ws):
+        S = np.abs(w.U0[:, 0]).max(axis=(1, 2)).reshape(-1, 1, 1, 1)
+        diff = max(diff, float((np.abs(served_out[q] - plain_out[q]) /
+                                np.maximum(np.abs(plain_out[q]), S)).max()))
+    cs = lambda st: st * n * 3
+    return {"workload": f"{tubes} seeded 1D Euler shock tubes, {n} cells each, T = {t_end}",
+            "steps": steps, "plain_fp64_loop": {"seconds": el_plain,
+                                                "cell_stages_per_s": cs(steps) / el_plain},
+            "batched": {"seconds": el_b, "cell_stages_per_s": cs(steps_b) / el_b},
+            "speedup": el_plain / el_b, "max_rel_diff_batched_vs_plain": diff,
+            "same_steps": steps_b == steps}
+
+
 def run_sweep(args):
     """Convergence of the FP64 and FP32-bulk paths on the periodic isentropic vortex
     (rho = p = 1, u = v = 1 plus the vortex, [0,1]^2, T = 0.05) against the exact translated
@@ -457,6 +511,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-tubes", action="store_true")
+    ap.add_argument("--tubes", type=int, default=16)
+    ap.add_argument("--tubes-n", type=int, default=4000)
+    ap.add_argument("--tubes-t", type=float, default=1.5)
     ap.add_argument("--served-m", type=int, default=16)
     ap.add_argument("--served-grids", default="128,256,384,512")
     ap.add_argument("--served-tlo", type=float, default=0.02)

@@ -6,8 +6,9 @@
 
 namespace hw {
 
-constexpr int kBatchBW = 128;     // threads per block of the batched stage kernel
-constexpr int kBatchClasses = 8;  // {advection, Burgers, Euler comp.-wise, Euler char.} x {FP64, mixed}
+constexpr int kBatchBW = 128;      // threads per block of the batched stage kernels
+constexpr int kBatchClasses = 16;  // {2D, 1D} x {advection, Burgers, Euler comp.-wise,
+                                   // Euler char.} x {FP64, mixed}
 
 // One solve in a batch (device-resident array, rewritten on admission / retirement).
 struct BatchSolve {
@@ -16,7 +17,7 @@ struct BatchSolve {
   double* Vh;
   DevScal* sc;
   int mixed;           // 1: FP32 bulk / FP64 weights
-  int bands, wout, rows, chunks;
+  int bands, wout, rows, chunks;  // 1D: bands = blocks of kBatchBW - 2 cells, chunks = 1
   int item_base;       // first work item of the solve
 };
 
@@ -37,8 +38,9 @@ struct BatchDt {
   int dim[kBatchCap];
 };
 
-int batch_class(int equation, int characteristic, int mixed);
+int batch_class(int equation, int characteristic, int mixed, int dim = 2);
 void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks);
+void batch_geometry1d(int nx, int* blocks);
 int batch_slots(int cls);  // resident blocks of the class's persistent launch
 cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st);
 cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,

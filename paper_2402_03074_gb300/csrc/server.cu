@@ -7,8 +7,8 @@
 //      (allocation, upload, speeds of the initial state, entry in the device work lists);
 //   2. advances every live solve by a few time steps: one replay of a captured step graph =
 //      one batched dt launch (each solve its own dt) + per kernel class three persistent
-//      stage launches over the work items of all live 2D solves of that class (1D solves
-//      are advanced by their own step graph);
+//      stage launches over the work items of all live solves of that class (1D and 2D
+//      solves are separate classes);
 //   3. reads the scalars of all live solves back in one copy and retires the finished ones
 //      (result copied to host memory, device memory released, work lists rewritten).
 // Requests that arrive while others run are admitted at the next iteration: their work
@@ -112,7 +112,10 @@ static void server_free(Server* S) {
   cudaFreeHost(S->h_gather);
 }
 
-static bool batched(const hweno_problem* p) { return p->dim == 2; }
+static bool batched(const hweno_problem* p) { return p->dim == 1 || p->dim == 2; }
+static int class_of(const hweno_problem* p) {
+  return batch_class(p->equation, p->characteristic, p->precision == HWENO_MIXED32, p->dim);
+}
 
 static thread_local std::string g_srv_err;
 static int srv_fail(cudaError_t c, const char* what) {
@@ -125,7 +128,7 @@ static int srv_fail(cudaError_t c, const char* what) {
     if (_c != cudaSuccess) return srv_fail(_c, #call); \
   } while (0)
 
-// rewrite the device work lists from the live set (batched 2D solves first: the dt list
+// rewrite the device work lists from the live set (batched solves first: the dt list
 // covers them, the gather list covers every live solve in the same order as S->live)
 static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
   std::stable_partition(S->live.begin(), S->live.end(),
@@ -138,8 +141,8 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
   long long band_rows[kBatchClasses] = {};
   for (Request* r : S->live) {
     const hweno_problem* p = solve_problem(r->solve);
-    if (!batched(p)) continue;
-    const int cls = batch_class(p->equation, p->characteristic, p->precision == HWENO_MIXED32);
+    if (!batched(p) || p->dim != 2) continue;
+    const int cls = class_of(p);
     int bands, wout, chunks;
     batch_geometry(p->nx, p->ny, 1, &bands, &wout, &chunks);
     band_rows[cls] += (long long)bands * p->ny;
@@ -163,14 +166,21 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     ++nall;
     if (!batched(p)) continue;
     ++n;
-    const int cls = batch_class(p->equation, p->characteristic, p->precision == HWENO_MIXED32);
+    const int cls = class_of(p);
     BatchSolve& B = S->h_bs[cls * kBatchCap + nb[cls]];
     B.P = kp;
     solve_pointers(sv, &B.U[0], &B.U[1], &B.U[2], &B.Vh);
     B.sc = solve_scalars(sv);
     B.mixed = p->precision == HWENO_MIXED32;
-    B.rows = rows_of[cls];
-    batch_geometry(p->nx, p->ny, B.rows, &B.bands, &B.wout, &B.chunks);
+    if (p->dim == 2) {
+      B.rows = rows_of[cls];
+      batch_geometry(p->nx, p->ny, B.rows, &B.bands, &B.wout, &B.chunks);
+    } else {
+      batch_geometry1d(p->nx, &B.bands);
+      B.wout = kBatchBW - 2;
+      B.rows = 1;
+      B.chunks = 1;
+    }
     B.item_base = items[cls];
     items[cls] += B.bands * B.chunks;
     ++nb[cls];
@@ -283,15 +293,15 @@ static int serve_once(Server* S, long long max_steps) {
       if (rc) return rc;
     }
   }
-  // 1D solves: their own step graphs
+  // solves outside the batch classes (none at present): their own step graphs
   for (Request* r : S->live)
     if (!batched(&r->prob)) {
       long long n = 0;
       engine_run(e, r->solve, r->prob.t_end, max_steps, &n);
     }
-  bool any2d = false;
-  for (Request* r : S->live) any2d |= batched(&r->prob);
-  if (any2d) {
+  bool anyb = false;
+  for (Request* r : S->live) anyb |= batched(&r->prob);
+  if (anyb) {
     const long long reps = std::max<long long>(1, max_steps / 2);
     for (long long i = 0; i < reps; ++i) SRV_TRY(cudaGraphLaunch(S->graph, st));
   }

@@ -1,0 +1,177 @@
+// stage1d_item.cuh -- one block of the fused 1D HWENO-U stage (Sec. 2.1, Eq. 2.3, 2.4, 2.12,
+// 2.13), shared by the single-solve kernel (stage1d.cu) and the batched persistent kernel
+// (batch.cu).
+//
+// One thread per reconstructed cell.  Block blk of BW threads reconstructs cells
+// [i0-1, i0+BW-1), i0 = blk (BW-2), and updates the BW-2 cells [i0, i0+BW-2): every cell is
+// reconstructed once per block, every face flux is computed once (by the thread left of the
+// face) and shared through shared memory, so the two cells of a face see the same flux bits.
+#pragma once
+#include "hweno_device.cuh"
+
+namespace hw {
+
+template <int EQ, bool CHAR, typename R, int BW>
+__device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S, int blk) {
+  constexpr int NC = (EQ == EQ_EULER) ? 3 : 1;
+  constexpr int NM = 2;
+  const int nx = P.nx;
+  const int t = threadIdx.x;
+  const int i0 = blk * (BW - 2);
+  const int i = i0 - 1 + t;  // reconstructed cell of this thread
+
+  __shared__ double win[NC * NM][BW + 2];    // moments of cells i0-2 .. i0+BW-1
+  __shared__ R trL[NC][2][BW];               // left trace (u, f) of each thread's cell
+  __shared__ R fhat[NC][BW + 1];             // flux at the left face of thread t's cell
+  __shared__ double red[BW / 32];
+
+  // a1: load with boundary conditions
+  for (int q = t; q < NC * NM * (BW + 2); q += BW) {
+    const int a = q / (BW + 2), col = q % (BW + 2);
+    const int c = a / NM, m = a % NM;
+    int flip;
+    const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
+    double val = S.Uin[(size_t)a * nx + ii];
+    if (flip) val *= mirror_sign<EQ, 1>(c, m, 1, 0);
+    win[a][col] = val;
+  }
+  __syncthreads();
+
+  const bool need = (i <= nx);                 // cells beyond the right ring are idle
+  const bool upd = (t >= 1 && t <= BW - 2 && i < nx);
+  // a2-a7: reconstruction of cell i (columns t, t+1, t+2 of the window)
+  R pts[4][NC], vh[NC];
+  if (need) {
+    if constexpr (CHAR && EQ == EQ_EULER) {
+      Eig1<R> E;
+      E.init(P, (R)win[0][t + 1], (R)win[2][t + 1], (R)win[4][t + 1]);
+      R Wm[3], W0[3], Wp[3], Zm[3], Zp[3];
+      {
+        R Um[3] = {(R)win[0][t], (R)win[2][t], (R)win[4][t]};
+        R Uc[3] = {(R)win[0][t + 1], (R)win[2][t + 1], (R)win[4][t + 1]};
+        R Up[3] = {(R)win[0][t + 2], (R)win[2][t + 2], (R)win[4][t + 2]};
+        R Vm[3] = {(R)win[1][t], (R)win[3][t], (R)win[5][t]};
+        R Vp[3] = {(R)win[1][t + 2], (R)win[3][t + 2], (R)win[5][t + 2]};
+        E.project(Um, Wm);
+        E.project(Uc, W0);
+        E.project(Up, Wp);
+        E.project(Vm, Zm);
+        E.project(Vp, Zp);
+      }
+      R cp[4][3], cv[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        R p4[4], v;
+        recon1d<R>(Wm[f], W0[f], Wp[f], Zm[f], Zp[f], P, p4, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) cp[g][f] = p4[g];
+        cv[f] = v;
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) E.unproject(cp[g], pts[g]);
+      E.unproject(cv, vh);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        R p4[4], v;
+        recon1d<R>((R)win[c * NM][t], (R)win[c * NM][t + 1], (R)win[c * NM][t + 2],
+                   (R)win[c * NM + 1][t], (R)win[c * NM + 1][t + 2], P, p4, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) pts[g][c] = p4[g];
+        vh[c] = v;
+      }
+    }
+  }
+  // a9: physical fluxes at the four Gauss-Lobatto nodes (the end nodes are the traces)
+  R fp[4][NC];
+  if (need) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if constexpr (EQ == EQ_EULER) euler_flux<1, R>(P, 0, pts[g], fp[g]);
+      else Phys<EQ, R>::flux(P, 0, pts[g], fp[g]);
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      trL[c][0][t] = pts[0][c];
+      trL[c][1][t] = fp[0][c];
+    }
+  }
+  __syncthreads();
+  // a8: LF flux at the right face of cell i (Eq. 2.4), once per face
+  const R alpha = (R)S.alpha_in[0];
+  if (need && t < BW - 1 && i < nx) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const R uL = pts[3][c], fL = fp[3][c];
+      const R uR = trL[c][0][t + 1], fR = trL[c][1][t + 1];
+      fhat[c][t + 1] = R(0.5) * (fL + fR - alpha * (uR - uL));
+    }
+  }
+  __syncthreads();
+  // a10-a11: right-hand sides (Eq. 2.3) and the stage combination (Eq. 2.13)
+  double wmax = 0.0;
+  if (upd) {
+    const double dt = *S.dt;
+    const R idx = (R)P.inv_dx;
+    double outv[NC * NM];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const R fl = fhat[c][t], fr = fhat[c][t + 1];
+      const R F1 = -(fr - fl) * idx;
+      const R vol = R(1.0 / 12.0) * (fp[0][c] + fp[3][c]) + R(5.0 / 12.0) * (fp[1][c] + fp[2][c]);
+      const R F2 = (vol - R(0.5) * (fl + fr)) * idx;
+      const double own_u = win[c * NM][t + 1];
+      const double own_v = (double)vh[c];
+      const size_t q0 = (size_t)(c * NM) * nx + i, q1 = q0 + nx;
+      double base_u, base_v;
+      if (S.k == 1) {
+        base_u = own_u;
+        base_v = own_v;
+        S.Vh[(size_t)c * nx + i] = own_v;
+      } else {
+        base_u = S.Un[q0];
+        base_v = S.Vh[(size_t)c * nx + i];
+      }
+      const double au = fma(dt, (double)F1, own_u), av = fma(dt, (double)F2, own_v);
+      double ou, ov;
+      if (S.k == 1) { ou = au; ov = av; }
+      else if (S.k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
+      else { ou = fma(1.0 / 3.0, base_u, 2.0 / 3.0 * au); ov = fma(1.0 / 3.0, base_v, 2.0 / 3.0 * av); }
+      S.Uout[q0] = ou;
+      S.Uout[q1] = ov;
+      outv[c * NM] = ou;
+      outv[c * NM + 1] = ov;
+    }
+    // a12-a13: wave speed of the output average, physicality
+    double ua[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) ua[c] = outv[c * NM];
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < NC * NM; ++q) bad |= !isfinite(outv[q]);
+    if constexpr (EQ == EQ_EULER) {
+      bad |= !euler_physical<1>(P, ua);
+      if (!bad) wmax = euler_speed<1>(P, 0, ua);
+    } else {
+      wmax = Phys<EQ, double>::speed(P, 0, ua);
+    }
+    if (bad) {
+      atomicOr(S.status, 1u);
+      wmax = 0.0;
+    }
+  }
+  // block max -> one atomic per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if ((t & 31) == 0) red[t >> 5] = wmax;
+  __syncthreads();
+  if (t == 0) {
+    double m = red[0];
+#pragma unroll
+    for (int w = 1; w < BW / 32; ++w) m = fmax(m, red[w]);
+    atomic_max_nonneg(&S.alpha_out[0], m);
+  }
+  __syncthreads();  // the block may start another item in the same shared memory
+}
+
+}  // namespace hw

@@ -7,7 +7,8 @@ namespace hw {
 
 // single-solve kernel: one block per (band, chunk)
 template <int EQ, bool CHAR, typename R, int BW>
-__global__ void __launch_bounds__(BW, 1) stage2d_kernel(KProblem P, KStage S, int rows, int wout) {
+__global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
+    stage2d_kernel(KProblem P, KStage S, int rows, int wout) {
   if (S.active && *S.active == 0) return;
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];

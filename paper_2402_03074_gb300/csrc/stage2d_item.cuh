@@ -17,6 +17,13 @@
 namespace hw {
 
 
+// Resident blocks per SM the 2D stage kernels are compiled for: the FP64 kernels take the
+// whole register file at two blocks per SM (255 registers per thread), the FP32-bulk kernels
+// three (at most 170 registers per thread, a few hundred bytes of spills), which hides more
+// of the FP64 latency of their weight evaluation.
+template <typename R>
+constexpr int kMinBlocks2D = sizeof(R) == 4 ? 3 : 1;
+
 // Gauss weights on [-1/2, 1/2] (sum 1) and nodes
 #define GW0 (5.0 / 18.0)
 #define GW1 (4.0 / 9.0)
@@ -48,11 +55,13 @@ __device__ __forceinline__ void volume_sum(const KProblem& P, int dir, const R (
 // One work item: band `band` (output columns band*wout .. +wout-1) and row chunk `chunk`
 // (output rows chunk*rows .. +rows-1) of one stage of one solve, processed by a whole block.
 // smem: dynamic shared memory of smem_bytes2d<EQ, R, BW>(); red: 2*(BW/32) doubles.
+// The row window holds the stage input in the bulk precision R (converted once per value
+// when a row is loaded); the FP64 update reads the cell's own averages from global memory
+// when R is float.
 template <int EQ, typename R, int BW>
 constexpr size_t smem_bytes2d() {
   constexpr int NC = (EQ == EQ_EULER) ? 4 : 1;
-  return sizeof(double) * 4 * NC * 3 * (BW + 2) + sizeof(R) * NC * 3 * 2 * BW +
-         sizeof(R) * NC * 3 * BW;
+  return sizeof(R) * 4 * NC * 3 * (BW + 2) + sizeof(R) * NC * 3 * 2 * BW;
 }
 
 template <int EQ, bool CHAR, typename R, int BW>
@@ -63,9 +72,12 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   constexpr int NM = 3;
   constexpr int NA = NC * NM;
   constexpr int WC = BW + 2;  // window columns: global columns i0-2 .. i0+BW-1
-  double* win = smem;                                   // [4 rows][NA][WC]
-  R* trL = reinterpret_cast<R*>(win + 4 * NA * WC);     // [NC][3][2][BW]
-  R* fhx = trL + NC * 3 * 2 * BW;                        // [NC][3][BW]: left face of thread t
+  R* win = reinterpret_cast<R*>(smem);                  // [4 rows][NA][WC]
+  // x-face exchange, [NC][3][2][BW]: the left trace u and its flux f of every thread's cell;
+  // the face flux at the left face of thread x's cell then overwrites the u slot x (its only
+  // reader, thread x - 1, has read it by then)
+  R* trL = win + 4 * NA * WC;
+  auto fhx = [&](int cg, int x) -> R& { return trL[(cg * 2 + 0) * BW + x]; };
 
   const int nx = P.nx, ny = P.ny;
   const size_t plane = (size_t)nx * ny;
@@ -84,14 +96,14 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   auto load_row = [&](int r) {
     int fy;
     const int rr = bc_map(r, ny, P.bc[2], P.bc[3], fy);
-    double* dst = win + (r & 3) * NA * WC;
+    R* dst = win + (r & 3) * NA * WC;
     for (int q = t; q < NA * WC; q += BW) {
       const int a = q / WC, col = q - a * WC;
       int fx;
       const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], fx);
       double val = S.Uin[(size_t)a * plane + (size_t)rr * nx + ii];
       if (fx | fy) val *= mirror_sign<EQ, 2>(a / NM, a % NM, fx, fy);
-      dst[a * WC + col] = val;
+      dst[a * WC + col] = (R)val;
     }
   };
 #pragma unroll 1
@@ -106,12 +118,12 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
 
 #pragma unroll 1
   for (int j = j0 - 1; j <= j1; ++j) {
-    const double* wm = win + ((j - 1) & 3) * NA * WC;
-    const double* w0 = win + (j & 3) * NA * WC;
-    const double* wp = win + ((j + 1) & 3) * NA * WC;
+    const R* wm = win + ((j - 1) & 3) * NA * WC;
+    const R* w0 = win + (j & 3) * NA * WC;
+    const R* wp = win + ((j + 1) & 3) * NA * WC;
     auto Wv = [&](int a, int k) -> R {   // moment array a of stencil cell k (0..8)
-      const double* rowp = (k < 3) ? wm : (k < 6 ? w0 : wp);
-      return (R)rowp[a * WC + t + (k % 3)];
+      const R* rowp = (k < 3) ? wm : (k < 6 ? w0 : wp);
+      return rowp[a * WC + t + (k % 3)];
     };
     const bool xrow = (j >= j0 && j < j1);
 
@@ -145,17 +157,16 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           for (int c = 0; c < NC; ++c) {
             const R uR = trL[((c * 3 + g) * 2 + 0) * BW + t + 1];
             const R fR = trL[((c * 3 + g) * 2 + 1) * BW + t + 1];
-            fhx[(c * 3 + g) * BW + t + 1] = R(0.5) * (fr[g][c] + fR - a1 * (uR - xr[g][c]));
+            fhx(c * 3 + g, t + 1) = R(0.5) * (fr[g][c] + fR - a1 * (uR - xr[g][c]));
           }
       }
       __syncthreads();
       if (outc) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          const R L0 = fhx[(c * 3 + 0) * BW + t], L1 = fhx[(c * 3 + 1) * BW + t],
-                  L2 = fhx[(c * 3 + 2) * BW + t];
-          const R R0 = fhx[(c * 3 + 0) * BW + t + 1], R1 = fhx[(c * 3 + 1) * BW + t + 1],
-                  R2 = fhx[(c * 3 + 2) * BW + t + 1];
+          const R L0 = fhx(c * 3 + 0, t), L1 = fhx(c * 3 + 1, t), L2 = fhx(c * 3 + 2, t);
+          const R R0 = fhx(c * 3 + 0, t + 1), R1 = fhx(c * 3 + 1, t + 1),
+                  R2 = fhx(c * 3 + 2, t + 1);
           const R sdiff = R(GW0) * ((R0 - L0) + (R2 - L2)) + R(GW1) * (R1 - L1);
           const R ssum = R(GW0) * ((L0 + R0) + (L2 + R2)) + R(GW1) * (L1 + R1);
           const R smom = R(GW0) * s15 * ((R2 - L2) - (R0 - L0));
@@ -340,7 +351,10 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
         double outv[NC * NM];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          const double own[3] = {wm[(c * NM) * WC + t + 1], (double)pvh[c], (double)pwh[c]};
+          const double own_u = (sizeof(R) == sizeof(double))
+                                   ? (double)wm[(c * NM) * WC + t + 1]
+                                   : S.Uin[(size_t)(c * NM) * plane + q];
+          const double own[3] = {own_u, (double)pvh[c], (double)pwh[c]};
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
             const size_t qa = (size_t)(c * NM + m) * plane + q;

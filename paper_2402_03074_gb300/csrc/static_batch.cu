@@ -55,7 +55,8 @@ __global__ void static_setup_kernel(StaticScratch* dst, StaticScratch src) {
 }
 
 template <int EQ, bool CHAR, typename R, int BW>
-__global__ void __launch_bounds__(BW, 1) static_batch_kernel(StaticScratch* sc, int k) {
+__global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
+    static_batch_kernel(StaticScratch* sc, int k) {
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];
   __shared__ int item_s;

@@ -8,7 +8,7 @@
   times, FP64 results within 1e-12 of the component scale, FP32-bulk results within 1e-4
   (FP32 rounding differences, amplified by the nonlinear weights over tens of steps).
 * Admission under a memory budget, poll semantics, the background serving thread, a served
-  solve against the FP64 oracle, and 1D and 2D requests together."""
+  solve against the FP64 oracle, 1D and 2D requests together, and batched 1D shock tubes."""
 import time
 
 import numpy as np
@@ -216,5 +216,39 @@ def test_served_1d_and_2d_together():
         res = _serve_all(eng, [t1, t2], {t1: w1.U0.shape, t2: w2.U0.shape})
     finally:
         H.hweno_destroy(eng)
-    np.testing.assert_array_equal(res[t1][0], _solo(p1, w1.U0, 0.05)[0])   # same 1D kernel
+    _same(res[t1][0], _solo(p1, w1.U0, 0.05)[0])
     _same(res[t2][0], _solo(p2, w2.U0, 0.02)[0])
+
+
+def _tube(seed, n=600, T=0.05, precision=H.HWENO_FP64):
+    w = I.shock_tube_1d(seed, n=n, t_end=T)
+    p = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc,
+                       t_end=T, precision=precision)
+    return w, p, T
+
+
+def test_served_1d_tubes_batched():
+    """Sixteen 1D shock tubes of uneven sizes advanced together by the batched 1D launches:
+    each result equals the same tube served alone bitwise, and the single-solve path within
+    the parity tolerance (same steps and time)."""
+    reqs = [_tube(sd, n=300 + 97 * sd, precision=H.HWENO_MIXED32 if sd % 5 == 4 else H.HWENO_FP64)
+            for sd in range(16)]
+    mix = _served(reqs)
+    for (w, p, T), (out, info) in zip(reqs, mix):
+        alone, ainfo = _served([(w, p, T)])[0]
+        np.testing.assert_array_equal(out, alone)
+        assert info.steps == ainfo.steps and info.t == T
+        solo, t, n = _solo(p, w.U0, T)
+        assert info.steps == n and t == T
+        _same(out, solo, precision=p.precision)
+
+
+def test_served_1d_tube_matches_oracle():
+    w, p, T = _tube(7, n=400)
+    op = O.Problem(dim=1, eq=O.EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
+    out, info = _served([(w, p, T)])[0]
+    ref, t, ns, st = O.run(op, w.U0, 0.0, T)
+    assert info.steps == ns and st == 0
+    S = np.abs(w.U0[:, 0]).max(axis=(1, 2))[:, None, None, None]
+    err = (np.abs(out - ref) / np.maximum(np.abs(ref), S)).max()
+    assert err <= 1e-12 * ns
