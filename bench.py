@@ -41,9 +41,14 @@ FP32_PEAK_TFLOPS = 74.2
 # redundant ring-cell reconstruction (profiles/stage2d_euler_2048_instruction_counts.md)
 FP64_FLOPS_PER_CELL_STAGE = 5529.0
 # DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
-FP64_STAGE_DRAM_BYTES = 425.9e6 + 673.2e6
+FP64_STAGE_DRAM_BYTES = 425.7e6 + 669.4e6
 # FP64 pipe utilisation of the same kernel (same capture, % of peak sustained, active cycles)
 FP64_PIPE_UTIL_NCU = 0.856
+# FP32-bulk kernel (same workload, ncu): FP64-pipe thread slots (FP64 arithmetic, f32 <-> f64
+# conversions, compares) and FP32 flops per cell-stage; the FP64 pipe issues one thread slot
+# per lane per clock, i.e. half the FP64 FMA flop rate
+FP32BULK_FP64_SLOTS_PER_CELL_STAGE = 1321.0
+FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4250.0
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
@@ -237,31 +242,36 @@ def run_ours(args):
     value = replica_throughput(cell_stages, ms64, world)
 
     # the fused stage kernel alone: per-launch duration from events on its stream
-    p64 = prob(H.HWENO_FP64)
     d = torch.device("cuda", dev)
-    Ud = torch.from_numpy(U0).to(d)
-    Uo = torch.empty_like(Ud)
-    Vh = torch.zeros((4, 2, n, n), dtype=torch.float64, device=d)
-    a_in = torch.zeros(2, dtype=torch.float64, device=d)
-    H.hweno_alpha_device(p64, Ud, a_in, torch.cuda.current_stream().cuda_stream)
-    a_out = torch.zeros(2, dtype=torch.float64, device=d)
-    torch.cuda.synchronize()
-    dtv = 0.6 / ((a_in[0] + a_in[1]).item() * n)
-    dtt = torch.tensor([dtv], dtype=torch.float64, device=d)
-    st = torch.zeros(1, dtype=torch.int32, device=d)
-    ks = torch.cuda.Stream(device=d)
-    kernel_ms = []
-    with torch.cuda.stream(ks):
-        for rep in range(args.kernel_reps + 1):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(ks)
-            H.hweno_stage_device(p64, 1, Ud, Ud, Vh, Uo, a_in, a_out, dtt, st, ks.cuda_stream)
-            e1.record(ks)
-            e1.synchronize()
-            if rep > 0:
-                kernel_ms.append(e0.elapsed_time(e1))
-    k_ms = statistics.mean(kernel_ms)
-    del Ud, Uo, Vh
+
+    def stage_kernel_ms(p):
+        Ud = torch.from_numpy(U0).to(d)
+        Uo = torch.empty_like(Ud)
+        Vh = torch.zeros((4, 2, n, n), dtype=torch.float64, device=d)
+        a_in = torch.zeros(2, dtype=torch.float64, device=d)
+        H.hweno_alpha_device(p, Ud, a_in, torch.cuda.current_stream().cuda_stream)
+        a_out = torch.zeros(2, dtype=torch.float64, device=d)
+        torch.cuda.synchronize()
+        dtv = 0.6 / ((a_in[0] + a_in[1]).item() * n)
+        dtt = torch.tensor([dtv], dtype=torch.float64, device=d)
+        st = torch.zeros(1, dtype=torch.int32, device=d)
+        ks = torch.cuda.Stream(device=d)
+        times = []
+        with torch.cuda.stream(ks):
+            for rep in range(args.kernel_reps + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(ks)
+                H.hweno_stage_device(p, 1, Ud, Ud, Vh, Uo, a_in, a_out, dtt, st, ks.cuda_stream)
+                e1.record(ks)
+                e1.synchronize()
+                if rep > 0:
+                    times.append(e0.elapsed_time(e1))
+        del Ud, Uo, Vh
+        return statistics.mean(times)
+
+    p64 = prob(H.HWENO_FP64)
+    k_ms = stage_kernel_ms(p64)
 
     # FP32-bulk / FP64-weights path on identical inputs
     mixed = None
@@ -269,8 +279,18 @@ def run_ours(args):
         ms32, out32 = timed_steps(H.HWENO_MIXED32, args.steps, args.warmup)
         diff = np.abs(out32[:, 0] - out64[:, 0])
         scale = np.abs(out64[:, 0]).mean(axis=(1, 2))[:, None, None]
+        k32_ms = stage_kernel_ms(prob(H.HWENO_MIXED32))
+        slots = FP32BULK_FP64_SLOTS_PER_CELL_STAGE * n * n / (k32_ms / 1e3)
         mixed = {"value": world * cell_stages / (ms32 / 1e3), "unit": UNIT, "dtype": "f32+f64",
                  "ms_per_step": ms32 / args.steps,
+                 "roofline": {"bound": "fp64 pipe", "kernel_ms": k32_ms,
+                              "fp64_pipe_slots_per_cell_stage": FP32BULK_FP64_SLOTS_PER_CELL_STAGE,
+                              "achieved_slots_per_s": slots,
+                              "peak_slots_per_s": FP64_PEAK_TFLOPS * 1e12 / 2.0,
+                              "frac": slots / (FP64_PEAK_TFLOPS * 1e12 / 2.0),
+                              "fp32_tflops": FP32BULK_FP32_FLOPS_PER_CELL_STAGE * n * n /
+                                             (k32_ms / 1e3) / 1e12,
+                              "fp32_peak_tflops": FP32_PEAK_TFLOPS},
                  "l1_vs_fp64": float((diff / scale).mean()),
                  "linf_vs_fp64": float((diff / scale).max()),
                  "error_note": "relative to the mean |average| of each component, after the "

@@ -74,17 +74,32 @@ __device__ __forceinline__ double mirror_sign(int c, int m, int fx, int fy) {
 }
 
 // Reciprocal 1/x: Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
-// seeded with the single-precision reciprocal of x; two steps take the 2^-22 relative error
-// of the seed below 2^-52 (result within 1 ulp of 1/x).  Values whose exponent is outside
-// +-100 of 1 (where the float seed could over- or underflow) use the division.
+// seeded with the single-precision reciprocal of x; two steps take the < 2^-22 relative error
+// of the seed below 2^-52 (result within 1 ulp of 1/x).  The double <-> float format changes
+// of the seed are done on the integer bits (x's significand truncated to 23 bits; the float
+// result widened exactly), so only the four FMAs use the FP64 pipe.  Values whose exponent is
+// outside +-100 of 1 (where the float seed could over- or underflow) use the division.
 __device__ __forceinline__ double rcp_nr(double x) {
-  const long long eb = (__double_as_longlong(x) >> 52) & 0x7ff;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ff);
   if (eb < 1023 - 100 || eb > 1023 + 100) return 1.0 / x;
-  double y = (double)__frcp_rn((float)x);
+  const unsigned int xf = (unsigned int)(b >> 32) & 0x80000000u |
+                          (unsigned int)(eb - 1023 + 127) << 23 |
+                          (unsigned int)(b >> 29) & 0x7fffffu;
+  const unsigned int rf = __float_as_uint(__frcp_rn(__uint_as_float(xf)));
+  const unsigned long long yb = (unsigned long long)(rf & 0x80000000u) << 32 |
+                                (unsigned long long)((rf >> 23 & 0xffu) - 127u + 1023u) << 52 |
+                                (unsigned long long)(rf & 0x7fffffu) << 29;
+  double y = __longlong_as_double((long long)yb);
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);
   return fma(y, e, y);
+}
+
+// finiteness from the exponent bits (integer pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
 }
 template <typename R>
 __device__ __forceinline__ R rcp(R x) { return R(1) / x; }
@@ -489,7 +504,7 @@ __device__ __forceinline__ bool euler_speeds(const KProblem& P, const double* u,
   const double vx = u[1] * ir;
   const double vy = DIM == 2 ? u[2] * ir : 0.0;
   const double e = u[DIM + 1] - 0.5 * (DIM == 2 ? fma(u[1], vx, u[2] * vy) : u[1] * vx);
-  const bool ok = u[0] > 0.0 && e > 0.0 && isfinite(e);
+  const bool ok = u[0] > 0.0 && e > 0.0 && finite_bits(e);
   const double c = sqrt(P.gam * ((P.gam - 1.0) * e) * ir);
   s0 = fabs(vx) + c;
   s1 = fabs(vy) + c;

@@ -379,7 +379,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
         for (int c = 0; c < NC; ++c) ua[c] = outv[c * NM];
         bool bad = false;
 #pragma unroll
-        for (int q2 = 0; q2 < NC * NM; ++q2) bad |= !isfinite(outv[q2]);
+        for (int q2 = 0; q2 < NC * NM; ++q2) bad |= !finite_bits(outv[q2]);
         if constexpr (EQ == EQ_EULER) {
           double s0, s1;
           bad |= !euler_speeds<2>(P, ua, s0, s1);
