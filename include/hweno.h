@@ -96,6 +96,11 @@ typedef struct hweno_result {
   double t;                 /* simulated time reached */
   int64_t steps;            /* time steps taken */
   double t_arrive, t_admit, t_finish; /* host wall-clock seconds (CLOCK_MONOTONIC) */
+  /* max over components c of |S_c(t) - S_c(0)| / A_c(0), S_c = sum of the cell averages of c
+     times the cell area, A_c the same sum of magnitudes (0 to round-off for periodic
+     boundaries, where the scheme is conservative, Eq. 2.3 / 2.16; the net boundary flux
+     otherwise).  Set when the solve has finished. */
+  double conservation_drift;
 } hweno_result;
 
 typedef struct hweno_engine hweno_engine;
@@ -123,6 +128,13 @@ int hweno_open(hweno_engine* eng, const hweno_problem* p, const double* moments_
 int hweno_set_state(hweno_engine* eng, uint64_t id, const double* moments_host, double t);
 /* Copy the moments and the time out (either pointer may be NULL). */
 int hweno_get_state(hweno_engine* eng, uint64_t id, double* moments_host, double* t);
+/* Conservation sums of the current state (diagnostic; not part of a step): for every
+   component c, sums[c] = S_c = (sum over cells of the cell average of c) x cell area (dx dy
+   in 2D, dx in 1D) and abs_sums[c] = the same sum of magnitudes (abs_sums may be NULL).
+   Both are host arrays of hweno_ncomp(p) doubles.  The scheme changes S_c only by the net
+   flux through the domain boundary (Eq. 2.3 / 2.16; zero for periodic boundaries).
+   Computed in FP64 by a fixed-order reduction (the same bits on every call). */
+int hweno_conservation(hweno_engine* eng, uint64_t id, double* sums, double* abs_sums);
 /* One full SSP-RK3 step (three stages, Eq. 2.13); dt from the CFL rule or dt_fixed.
    *dt_taken (may be NULL) receives the step.  Returns HWENO_ERR_NONPHYSICAL if the new state
    has rho <= 0, p <= 0 or non-finite values (the state is kept as computed). */

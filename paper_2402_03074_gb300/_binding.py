@@ -52,7 +52,7 @@ class hweno_engine_config(ctypes.Structure):
 class hweno_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("t", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("t_arrive", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_finish", ctypes.c_double)]
+                ("t_finish", ctypes.c_double), ("conservation_drift", ctypes.c_double)]
 
 
 def make_problem(dim=2, equation=HWENO_EULER, nx=16, ny=None, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
@@ -96,6 +96,7 @@ def lib() -> ctypes.CDLL:
             "hweno_open": ([E, P, dp, ctypes.POINTER(u64)], ctypes.c_int),
             "hweno_set_state": ([E, u64, dp, ctypes.c_double], ctypes.c_int),
             "hweno_get_state": ([E, u64, dp, dp], ctypes.c_int),
+            "hweno_conservation": ([E, u64, dp, dp], ctypes.c_int),
             "hweno_step": ([E, u64, dp], ctypes.c_int),
             "hweno_advance": ([E, u64, ctypes.c_double, ctypes.c_int64,
                                ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -174,6 +175,15 @@ def hweno_get_state(eng, sid: int, out: np.ndarray):
     t = ctypes.c_double()
     _check(lib().hweno_get_state(eng, sid, _host(out), ctypes.byref(t)), eng)
     return out, t.value
+
+
+def hweno_conservation(eng, sid: int, ncomp: int):
+    """(S, A): per component the sum of the cell averages times the cell area, and the same
+    sum of magnitudes, of the solve's current state."""
+    S = np.zeros(ncomp)
+    A = np.zeros(ncomp)
+    _check(lib().hweno_conservation(eng, sid, _host(S), _host(A)), eng)
+    return S, A
 
 
 def hweno_step(eng, sid: int) -> float:

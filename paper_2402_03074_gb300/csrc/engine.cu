@@ -196,6 +196,52 @@ double now_seconds() {
 
 // ------------------------------------------------------------------------------------
 // solves
+// Conservation sums (diagnostic): per component c, S_c = sum of the cell averages times the
+// cell area and A_c = sum of their magnitudes times the area.  Fixed-order reduction (each
+// block sums a contiguous slice, then one block sums the slices in order), so the result is
+// the same on every call for the same state.
+constexpr int kConsBlocks = 128;
+constexpr int kConsThreads = 256;
+__global__ void conservation_kernel(const double* U, long long ncell, int nm, double* partial) {
+  const int c = blockIdx.y;
+  const double* u = U + (size_t)(c * nm) * ncell;
+  const long long chunk = (ncell + gridDim.x - 1) / gridDim.x;
+  const long long q0 = blockIdx.x * chunk;
+  const long long q1 = q0 + chunk < ncell ? q0 + chunk : ncell;
+  double s = 0.0, a = 0.0;
+  for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    s += u[q];
+    a += fabs(u[q]);
+  }
+  __shared__ double rs[kConsThreads], ra[kConsThreads];
+  rs[threadIdx.x] = s;
+  ra[threadIdx.x] = a;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      rs[threadIdx.x] += rs[threadIdx.x + h];
+      ra[threadIdx.x] += ra[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * (c * gridDim.x + blockIdx.x)] = rs[0];
+    partial[2 * (c * gridDim.x + blockIdx.x) + 1] = ra[0];
+  }
+}
+__global__ void conservation_final_kernel(double* partial, int nb, int nc, double area) {
+  const int c = threadIdx.x;
+  if (c >= nc) return;
+  double s = 0.0, a = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    s += partial[2 * (c * nb + b)];
+    a += partial[2 * (c * nb + b) + 1];
+  }
+  // the totals follow the per-block slices: [2 * nc * nb + 2 c] = S_c, [.. + 1] = A_c
+  partial[2 * nc * nb + 2 * c] = s * area;
+  partial[2 * nc * nb + 2 * c + 1] = a * area;
+}
+
 struct Solve {
   hweno_problem prob;
   KProblem kp;
@@ -207,6 +253,8 @@ struct Solve {
   double* Vh = nullptr;
   DevScal* sc = nullptr;
   DevScal* host = nullptr;  // pinned mirror of the scalars
+  double* cons = nullptr;   // conservation-sum scratch: 2 nc kConsBlocks partials + 2 nc totals
+  double* cons_host = nullptr;  // pinned copy of the 2 nc totals
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   size_t bytes = 0;
@@ -215,7 +263,8 @@ struct Solve {
 size_t solve_bytes(const hweno_problem* p) {
   const size_t ncell = (size_t)p->nx * p->ny;
   const int nc = ncomp_of(p), nm = nmom_of(p);
-  return sizeof(double) * ncell * (size_t)(3 * nc * nm + nc * (nm - 1)) + sizeof(DevScal);
+  return sizeof(double) * ncell * (size_t)(3 * nc * nm + nc * (nm - 1)) + sizeof(DevScal) +
+         sizeof(double) * 2 * nc * (kConsBlocks + 1);
 }
 
 void solve_free(Solve* s) {
@@ -227,6 +276,8 @@ void solve_free(Solve* s) {
   cudaFree(s->Vh);
   cudaFree(s->sc);
   cudaFreeHost(s->host);
+  cudaFree(s->cons);
+  cudaFreeHost(s->cons_host);
   delete s;
 }
 
@@ -364,6 +415,8 @@ int engine_alloc_solve(hweno_engine* e, const hweno_problem* p, Solve** out) {
   if (c == cudaSuccess) c = cudaMalloc(&s->Vh, sizeof(double) * s->nV);
   if (c == cudaSuccess) c = cudaMalloc(&s->sc, sizeof(DevScal));
   if (c == cudaSuccess) c = cudaMallocHost(&s->host, sizeof(DevScal));
+  if (c == cudaSuccess) c = cudaMalloc(&s->cons, sizeof(double) * 2 * s->nc * (kConsBlocks + 1));
+  if (c == cudaSuccess) c = cudaMallocHost(&s->cons_host, sizeof(double) * 2 * s->nc);
   if (c != cudaSuccess) {
     solve_free(s);
     cudaGetLastError();
@@ -410,6 +463,26 @@ int engine_set_target(hweno_engine* e, Solve* s, double t_end, long long step_li
                               cudaMemcpyHostToDevice, st));
   CUDA_TRY(e, cudaMemcpyAsync(&s->sc->step_limit, &s->host->step_limit, sizeof(long long),
                               cudaMemcpyHostToDevice, st));
+  return HWENO_OK;
+}
+
+// conservation sums of U^n: sums[c] = S_c, abs_sums[c] = A_c (host arrays of nc doubles)
+int engine_conservation(hweno_engine* e, Solve* s, double* sums, double* abs_sums,
+                        cudaStream_t st) {
+  const double area = s->prob.dim == 2 ? ((s->prob.x1 - s->prob.x0) / s->prob.nx) *
+                                              ((s->prob.y1 - s->prob.y0) / s->prob.ny)
+                                        : (s->prob.x1 - s->prob.x0) / s->prob.nx;
+  conservation_kernel<<<dim3(kConsBlocks, s->nc), kConsThreads, 0, st>>>(
+      s->U0, (long long)s->ncell, s->nm, s->cons);
+  conservation_final_kernel<<<1, 32, 0, st>>>(s->cons, kConsBlocks, s->nc, area);
+  CUDA_TRY(e, cudaGetLastError());
+  CUDA_TRY(e, cudaMemcpyAsync(s->cons_host, s->cons + 2 * s->nc * kConsBlocks,
+                              sizeof(double) * 2 * s->nc, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(e, cudaStreamSynchronize(st));
+  for (int c = 0; c < s->nc; ++c) {
+    if (sums) sums[c] = s->cons_host[2 * c];
+    if (abs_sums) abs_sums[c] = s->cons_host[2 * c + 1];
+  }
   return HWENO_OK;
 }
 
@@ -556,6 +629,15 @@ int hweno_get_state(hweno_engine* e, uint64_t id, double* host, double* t) {
   if (rc) return rc;
   if (t) *t = s->host->t;
   return HWENO_OK;
+}
+
+int hweno_conservation(hweno_engine* e, uint64_t id, double* sums, double* abs_sums) {
+  if (!e || !sums) return fail(e, HWENO_ERR_ARG, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  Solve* s = engine_find(e, id);
+  if (!s) return fail(e, HWENO_ERR_ARG, "unknown solve id");
+  return engine_conservation(e, s, sums, abs_sums, e->stream);
 }
 
 int hweno_step(hweno_engine* e, uint64_t id, double* dt_taken) {

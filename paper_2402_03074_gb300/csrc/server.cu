@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <condition_variable>
 #include <cstring>
@@ -40,6 +41,8 @@ struct Request {
   double t = 0.0;
   long long steps = 0;
   double t_arrive = 0, t_admit = 0, t_finish = 0;
+  double cons0[4] = {}, abs0[4] = {};  // conservation sums of the initial state
+  double drift = 0.0;
   std::vector<double> result;
 };
 
@@ -238,6 +241,18 @@ static int ensure_batch_graph(Server* S, unsigned classes, cudaStream_t st) {
 static void finish(Server* S, Request* r, int rc) {
   r->t = solve_time(r->solve);
   if (rc == HWENO_OK) {
+    // conservation drift of the solve: max over components of |S_c(T) - S_c(0)| / A_c(0)
+    double s1[4] = {}, a1[4] = {};
+    rc = engine_conservation(S->eng, r->solve, s1, a1, engine_stream(S->eng));
+    const int nc = hweno_ncomp(&r->prob);
+    double d = 0.0;
+    for (int c = 0; c < nc && rc == HWENO_OK; ++c) {
+      const double den = r->abs0[c] > 0.0 ? r->abs0[c] : 1.0;
+      d = std::max(d, std::fabs(s1[c] - r->cons0[c]) / den);
+    }
+    r->drift = d;
+  }
+  if (rc == HWENO_OK) {
     const size_t n = (size_t)r->prob.nx * r->prob.ny * hweno_ncomp(&r->prob) * hweno_nmom(&r->prob);
     r->result.resize(n);
     rc = solve_copy_out(S->eng, r->solve, r->result.data());
@@ -262,6 +277,7 @@ static void admit(Server* S, cudaStream_t st) {
       continue;
     }
     rc = engine_load_state(S->eng, sv, r->init.data(), 0.0, st);
+    if (rc == HWENO_OK) rc = engine_conservation(S->eng, sv, r->cons0, r->abs0, st);
     if (rc == HWENO_OK) rc = engine_set_target(S->eng, sv, r->prob.t_end, 1LL << 62, st);
     if (rc) {
       engine_release_solve(S->eng, sv);
@@ -439,6 +455,7 @@ int hweno_poll(hweno_engine* e, uint64_t ticket, double* out, hweno_result* info
     info->t_arrive = r->t_arrive;
     info->t_admit = r->t_admit;
     info->t_finish = r->t_finish;
+    info->conservation_drift = r->drift;
   }
   const int st = r->status;
   if (st == HWENO_OK && out) {

@@ -24,6 +24,8 @@ int engine_load_state(hweno_engine* e, Solve* s, const double* host, double t, c
 int engine_set_target(hweno_engine* e, Solve* s, double t_end, long long step_limit,
                       cudaStream_t st);
 int engine_read_scalars(hweno_engine* e, Solve* s, cudaStream_t st);
+int engine_conservation(hweno_engine* e, Solve* s, double* sums, double* abs_sums,
+                        cudaStream_t st);
 int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps, long long* steps);
 cudaError_t enqueue_step(Solve* s, cudaStream_t st);
 std::recursive_mutex& engine_mutex(hweno_engine* e);

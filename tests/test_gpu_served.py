@@ -127,8 +127,9 @@ def test_served_mix_with_late_arrivals():
 def test_admission_by_memory_budget():
     w = I.quadrant_vortex_2d(7, 64)
     p = _prob2d(w, 0.01)
-    per_solve = 64 * 64 * 44 * 8 + 4096
-    eng = H.hweno_create(hbm_budget_bytes=2 * per_solve)     # room for two solves at a time
+    state_bytes = 64 * 64 * 44 * 8                           # U^n, U^(1), U^(2), V-hat
+    # room for two solves at a time (each also holds a few KB of scalars and scratch)
+    eng = H.hweno_create(hbm_budget_bytes=int(2.5 * state_bytes))
     try:
         tickets = [H.hweno_submit(eng, p, w.U0) for _ in range(5)]
         shapes = {tk: w.U0.shape for tk in tickets}
@@ -252,3 +253,34 @@ def test_served_1d_tube_matches_oracle():
     S = np.abs(w.U0[:, 0]).max(axis=(1, 2))[:, None, None, None]
     err = (np.abs(out - ref) / np.maximum(np.abs(ref), S)).max()
     assert err <= 1e-12 * ns
+
+
+def test_engine_shared_by_threads():
+    """One engine used from several host threads at once (calls are serialised inside the
+    engine): every solve advanced from its own thread gives bitwise the result of the same
+    solve advanced alone."""
+    import threading
+    ws = [I.quadrant_vortex_2d(20 + q, 48) for q in range(4)]
+    ps = [_prob2d(w, 0.02) for w in ws]
+    eng = H.hweno_create()
+    outs, errs = [None] * 4, []
+    try:
+        sids = [H.hweno_open(eng, p, w.U0) for w, p in zip(ws, ps)]
+
+        def work(q):
+            try:
+                H.hweno_advance(eng, sids[q], 0.02)
+                outs[q] = H.hweno_get_state(eng, sids[q], np.empty_like(ws[q].U0))[0]
+            except Exception as e:  # reported below
+                errs.append(e)
+
+        th = [threading.Thread(target=work, args=(q,)) for q in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join(timeout=120)
+    finally:
+        H.hweno_destroy(eng)
+    assert not errs, errs
+    for q in range(4):
+        np.testing.assert_array_equal(outs[q], _solo(ps[q], ws[q].U0, 0.02)[0])
