@@ -47,8 +47,8 @@ FP64_PIPE_UTIL_NCU = 0.856
 # FP32-bulk kernel (same workload, ncu): FP64-pipe thread slots (FP64 arithmetic, f32 <-> f64
 # conversions, compares) and FP32 flops per cell-stage; the FP64 pipe issues one thread slot
 # per lane per clock, i.e. half the FP64 FMA flop rate
-FP32BULK_FP64_SLOTS_PER_CELL_STAGE = 1321.0
-FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4250.0
+FP32BULK_FP64_SLOTS_PER_CELL_STAGE = 1091.0
+FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4291.0
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 

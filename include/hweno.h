@@ -206,13 +206,16 @@ int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
 
 /* ---- launch-geometry autotuner -------------------------------------------------------- */
 /* Time one fused stage launch of the 2D problem p on a scratch copy of moments_host for each
-   candidate height of the row chunks a block sweeps (the default one-wave geometry and 8,
-   16, 32, 64, 128, 256 rows), keep the fastest in the process-wide tuning table (keyed by
-   equation, characteristic decomposition, precision and grid) for every later single-solve
-   and batched launch of such problems, and report it (*best_rows: 0 = the default geometry;
-   *best_ms: one stage).  Either output pointer may be NULL. */
+   candidate tile shape -- the height of the row chunks a block sweeps (the default one-wave
+   geometry and 8, 16, 32, 64, 128, 256 rows) x the number of bands the columns are split into
+   (the widest bands of at most 126 columns, and 1.25, 1.5 and 2 times as many) -- keep the
+   fastest in the process-wide tuning table (keyed by equation, characteristic decomposition,
+   precision and grid) for every later single-solve launch of such problems, and report it
+   (*best_rows, *best_bands: 0 = the default; *best_ms: one stage).  Output pointers may be
+   NULL.  The tile shape changes no result bit (every cell and face is computed by the same
+   code in any decomposition). */
 int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* moments_host,
-                   int* best_rows, double* best_ms);
+                   int* best_rows, int* best_bands, double* best_ms);
 /* Save the tuning table as text (one entry per line, with the GPU name); load it back
    (entries of other GPUs are skipped).  hweno_tuning_load returns the entries loaded. */
 int hweno_tuning_save(const char* path);

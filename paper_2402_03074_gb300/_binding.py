@@ -107,7 +107,8 @@ def lib() -> ctypes.CDLL:
             "hweno_stage_device": ([P, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp],
                                    ctypes.c_int),
             "hweno_alpha_device": ([P, vp, vp, vp], ctypes.c_int),
-            "hweno_autotune": ([E, P, dp, ctypes.POINTER(ctypes.c_int), dp], ctypes.c_int),
+            "hweno_autotune": ([E, P, dp, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int), dp], ctypes.c_int),
             "hweno_stage_batch_static": ([ctypes.c_int, P, ctypes.c_int, vp, vp, vp, vp, vp, vp,
                                           vp, vp, vp], ctypes.c_int),
             "hweno_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
@@ -256,13 +257,15 @@ def hweno_engine_stream(eng) -> int:
 
 # ---- launch-geometry autotuner --------------------------------------------------------
 def hweno_autotune(eng, p: hweno_problem, U: np.ndarray):
-    """Returns (best rows per chunk (0 = default geometry), milliseconds of one stage)."""
+    """Returns (best rows per chunk, best band count (0 = the defaults), milliseconds of one
+    stage)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     rows = ctypes.c_int()
+    bands = ctypes.c_int()
     ms = ctypes.c_double()
     _check(lib().hweno_autotune(eng, ctypes.byref(p), _host(U), ctypes.byref(rows),
-                                ctypes.byref(ms)), eng)
-    return rows.value, ms.value
+                                ctypes.byref(bands), ctypes.byref(ms)), eng)
+    return rows.value, bands.value, ms.value
 
 
 def hweno_tuning_save(path: str) -> None:

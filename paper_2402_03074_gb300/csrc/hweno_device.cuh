@@ -97,6 +97,51 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// Format changes between float and double on the integer bits, for the FP32-bulk path, where
+// the FP64 weight evaluation takes its inputs from and returns its results to FP32 (the
+// hardware conversions issue on the FP64 pipe, the bound of that path).
+// float -> double: exact for normal numbers, zeros, infinities and NaNs; subnormal floats
+// (magnitude < 2^-126) become a zero of the same sign.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned int b = __float_as_uint(x);
+  const unsigned int e = (b >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned long long frac = (unsigned long long)(b & 0x7fffffu) << 29;
+  const unsigned long long mag = (unsigned long long)(e + 896u) << 52 | frac;
+  const unsigned long long r =
+      e == 0u ? sign : (e == 255u ? sign | 0x7ff0000000000000ull | frac : sign | mag);
+  return __longlong_as_double((long long)r);
+}
+// double -> float, rounded to nearest (ties to even) on the 63-bit exponent|fraction string:
+// exact for results in the normal float range; smaller magnitudes become a signed zero,
+// larger a signed infinity (NaN stays NaN).
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const unsigned long long t = b & 0x7fffffffffffffffull;
+  const unsigned long long rnd = (t + 0x0fffffffull + ((t >> 29) & 1ull)) >> 29;
+  const long long fb = (long long)rnd - (896ll << 23);
+  unsigned int r;
+  if ((t >> 52) == 0x7ffull)
+    r = sign | 0x7f800000u | (unsigned int)(t >> 29 & 0x7fffffu) |
+        ((t & 0xfffffffffffffull) ? 0x400000u : 0u);
+  else if (fb < (1ll << 23))
+    r = sign;
+  else if (fb >= (255ll << 23))
+    r = sign | 0x7f800000u;
+  else
+    r = sign | (unsigned int)fb;
+  return __uint_as_float(r);
+}
+template <typename R>
+__device__ __forceinline__ double to_f64(R x) { return (double)x; }
+template <>
+__device__ __forceinline__ double to_f64<float>(float x) { return f2d_bits(x); }
+template <typename R>
+__device__ __forceinline__ R from_f64(double x) { return (R)x; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }
+
 // finiteness from the exponent bits (integer pipe)
 __device__ __forceinline__ bool finite_bits(double x) {
   return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
@@ -192,7 +237,7 @@ __device__ __forceinline__ void recon1d(R um, R u0, R up, R vm, R vp, const KPro
   // Step 2: Eq. 2.9 (first term with c_{0,3}, from the definition Eq. 2.8)
   double beta[3];
   {
-    const double d1 = c1, d2 = c2, d3 = c3, d4 = c4;
+    const double d1 = to_f64(c1), d2 = to_f64(c2), d3 = to_f64(c3), d4 = to_f64(c4);
     const double t1 = fma(0.25, d3, d1);
     const double t2 = fma(63.0 / 130.0, d4, d2);
     double b = t1 * t1;
@@ -200,18 +245,18 @@ __device__ __forceinline__ void recon1d(R um, R u0, R up, R vm, R vp, const KPro
     b = fma(781.0 / 20.0 * d3, d3, b);
     b = fma(1421461.0 / 2275.0 * d4, d4, b);
     beta[0] = b;
-    const double e1 = l1, e2 = l2;
+    const double e1 = to_f64(l1), e2 = to_f64(l2);
     beta[1] = e1 * e1;
     beta[2] = e2 * e2;
   }
   // Step 3
-  const double a = ((double)fabs(um) + (double)fabs(u0) + (double)fabs(up)) * (1.0 / 3.0);
+  const double a = (to_f64(fabs(um)) + to_f64(fabs(u0)) + to_f64(fabs(up))) * (1.0 / 3.0);
   // combined polynomial u_i = a0 p_0 + sum_m (omega_m - a0 gamma_m) p_m, a0 = omega_0/gamma_0
   double a0d, bm[3];
   nonlinear_weights<3>(beta, a * a, P, a0d, bm);
-  const R a0 = (R)a0d;
-  const R b1 = (R)bm[1], b2 = (R)bm[2];
-  const R C0 = a0 * c0 + (R)(1.0 - a0d) * u0;
+  const R a0 = from_f64<R>(a0d);
+  const R b1 = from_f64<R>(bm[1]), b2 = from_f64<R>(bm[2]);
+  const R C0 = a0 * c0 + from_f64<R>(1.0 - a0d) * u0;
   const R C1 = a0 * c1 + b1 * l1 + b2 * l2;
   const R C2 = a0 * c2, C3 = a0 * c3, C4 = a0 * c4;
   // values at +-1/2 and +-sqrt(5)/10 (even / odd parts)
@@ -277,7 +322,7 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
   {
     double d[15];
 #pragma unroll
-    for (int n = 0; n < 15; ++n) d[n] = (double)c[n];
+    for (int n = 0; n < 15; ++n) d[n] = to_f64(c[n]);
     double s, t;
     t = fma(0.5, d[6], d[1]);
     s = t * t;
@@ -317,7 +362,7 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
     b = fma(31468281769.0 / 745051650.0 * d[13], d[13], b);
     b = fma(25118160529227568.0 / 40266452337475.0 * d[14], d[14], b);
     beta[0] = b;
-    const double el = dl, er = dr, eb = db, et = dtp;
+    const double el = to_f64(dl), er = to_f64(dr), eb = to_f64(db), et = to_f64(dtp);
     const double el2 = el * el, er2 = er * er, eb2 = eb * eb, et2 = et * et;
     beta[1] = el2 + eb2;
     beta[2] = er2 + eb2;
@@ -325,13 +370,14 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
     beta[4] = er2 + et2;
   }
   // Step 3
-  const double a = ((double)fabs(u2) + (double)fabs(u4) + (double)fabs(u5) + (double)fabs(u6) +
-                    (double)fabs(u8)) * 0.2;
+  const double a = (to_f64(fabs(u2)) + to_f64(fabs(u4)) + to_f64(fabs(u5)) + to_f64(fabs(u6)) +
+                    to_f64(fabs(u8))) * 0.2;
   double a0d, bm[5];
   nonlinear_weights<5>(beta, a * a, P, a0d, bm);
-  const R a0 = (R)a0d;
-  const R b1 = (R)bm[1], b2 = (R)bm[2], b3 = (R)bm[3], b4 = (R)bm[4];
-  C[0] = a0 * c[0] + (R)(1.0 - a0d) * u5;
+  const R a0 = from_f64<R>(a0d);
+  const R b1 = from_f64<R>(bm[1]), b2 = from_f64<R>(bm[2]), b3 = from_f64<R>(bm[3]),
+          b4 = from_f64<R>(bm[4]);
+  C[0] = a0 * c[0] + from_f64<R>(1.0 - a0d) * u5;
   C[1] = a0 * c[1] + (b1 + b3) * dl + (b2 + b4) * dr;
   C[2] = a0 * c[2] + (b1 + b2) * db + (b3 + b4) * dtp;
 #pragma unroll

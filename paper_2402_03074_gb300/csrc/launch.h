@@ -56,12 +56,19 @@ __device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_
   s->active = 1;
 }
 
-// Tuning table of the 2D launch geometry: rows per work item for (equation, characteristic,
-// precision, nx, ny); 0 = not tuned (one wave of blocks over the resident slots).
-int tuning_rows(int eq, int characteristic, int mixed, int nx, int ny);
-void tuning_set_rows(int eq, int characteristic, int mixed, int nx, int ny, int rows);
-// Rows-per-chunk override for the next 2D launches of this thread (autotuner), 0 = none.
-void tuning_force_rows(int rows);
+// Tile shape of the 2D single-solve launch: rows per chunk (tile height) and number of bands
+// (tile width = ceil(nx / bands) output columns); 0 = the default for that dimension (one
+// wave of blocks over the resident slots; the widest bands).
+struct TileShape {
+  int rows = 0;
+  int bands = 0;
+};
+// Tuning table keyed by (equation, characteristic, precision, nx, ny); {0, 0} = not tuned.
+TileShape tuning_shape(int eq, int characteristic, int mixed, int nx, int ny);
+void tuning_set_shape(int eq, int characteristic, int mixed, int nx, int ny, TileShape t);
+// Shape override for the next 2D launches of this thread (autotuner): rows / bands > 0 fix
+// them, -1 the default geometry ignoring the table, {0, 0} no override.
+void tuning_force_shape(TileShape t);
 
 // One stage of the modified SSP-RK3 over a whole grid (1D / 2D), asynchronous on st.
 cudaError_t launch_stage1d(int eq, bool characteristic, bool mixed, const KProblem& P,

@@ -17,14 +17,16 @@ __global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
 
 // Launch geometry: bands of equal width (<= BW-2 output columns) and row chunks sized so
 // that bands x chunks fills the resident block slots of the GPU once, unless the tuning
-// table (or the autotuner) fixes the rows per chunk.
+// table (or the autotuner) fixes the tile shape: rows per chunk and/or the band count.
 struct Geom2D {
   int bands, wout, chunks, rows;
 };
-static Geom2D geom2d(int nx, int ny, int bw, int slots, int rows_fixed) {
+static Geom2D geom2d(int nx, int ny, int bw, int slots, int rows_fixed, int bands_fixed) {
   Geom2D g;
-  g.bands = (nx + (bw - 2) - 1) / (bw - 2);
+  const int bmin = (nx + (bw - 2) - 1) / (bw - 2);
+  g.bands = bands_fixed > bmin ? (bands_fixed < nx ? bands_fixed : nx) : bmin;
   g.wout = (nx + g.bands - 1) / g.bands;
+  g.bands = (nx + g.wout - 1) / g.wout;  // no empty band
   if (rows_fixed > 0) {
     g.rows = rows_fixed < ny ? rows_fixed : ny;
   } else {
@@ -37,8 +39,8 @@ static Geom2D geom2d(int nx, int ny, int bw, int slots, int rows_fixed) {
   return g;
 }
 
-static thread_local int g_force_rows = 0;
-void tuning_force_rows(int rows) { g_force_rows = rows; }
+static thread_local TileShape g_force_shape;
+void tuning_force_shape(TileShape t) { g_force_shape = t; }
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t init2d_t(int* slots_out, size_t* local_out) {
@@ -73,9 +75,10 @@ static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t s
   int slots = 0;
   cudaError_t e = init2d_t<EQ, CHAR, R>(&slots, nullptr);
   if (e != cudaSuccess) return e;
-  int rows = g_force_rows;  // > 0 rows, -1 default geometry, 0 consult the table
-  if (rows == 0) rows = tuning_rows(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, P.ny);
-  const Geom2D g = geom2d(P.nx, P.ny, BW, slots, rows > 0 ? rows : 0);
+  TileShape t = g_force_shape;  // > 0 fixed, -1 default geometry, {0, 0} consult the table
+  if (t.rows == 0 && t.bands == 0)
+    t = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, P.ny);
+  const Geom2D g = geom2d(P.nx, P.ny, BW, slots, t.rows > 0 ? t.rows : 0, t.bands > 0 ? t.bands : 0);
   dim3 grid(g.bands, g.chunks);
   stage2d_kernel<EQ, CHAR, R, BW><<<grid, BW, smem_bytes2d<EQ, R, BW>(), st>>>(P, S, g.rows, g.wout);
   return cudaGetLastError();

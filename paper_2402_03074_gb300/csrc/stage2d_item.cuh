@@ -103,7 +103,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
       const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], fx);
       double val = S.Uin[(size_t)a * plane + (size_t)rr * nx + ii];
       if (fx | fy) val *= mirror_sign<EQ, 2>(a / NM, a % NM, fx, fy);
-      dst[a * WC + col] = (R)val;
+      dst[a * WC + col] = from_f64<R>(val);
     }
   };
 #pragma unroll 1
@@ -354,7 +354,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           const double own_u = (sizeof(R) == sizeof(double))
                                    ? (double)wm[(c * NM) * WC + t + 1]
                                    : S.Uin[(size_t)(c * NM) * plane + q];
-          const double own[3] = {own_u, (double)pvh[c], (double)pwh[c]};
+          const double own[3] = {own_u, to_f64(pvh[c]), to_f64(pwh[c])};
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
             const size_t qa = (size_t)(c * NM + m) * plane + q;
@@ -365,7 +365,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
             } else {
               base = (m == 0) ? S.Un[qa] : S.Vh[(size_t)(c * 2 + m - 1) * plane + q];
             }
-            const double adv = fma(dt, (double)pend[c][m], own[m]);
+            const double adv = fma(dt, to_f64(pend[c][m]), own[m]);
             double o;
             if (S.k == 1) o = adv;
             else if (S.k == 2) o = fma(0.75, base, 0.25 * adv);

@@ -1,11 +1,14 @@
 // tune.cu -- launch-geometry autotuner and its tuning table.
 //
-// The 2D stage kernel's blocks sweep row chunks of a band; taller chunks waste fewer ring
-// rows, shorter ones balance better over the SMs.  The autotuner times one stage launch of a
-// problem for each candidate chunk height on a scratch copy of the caller's moments, keeps
-// the fastest in a process-wide table keyed by (equation, characteristic decomposition,
-// precision, grid) and the table is consulted by every later launch (single-solve and
-// batched).  The table can be saved and loaded as text; entries carry the GPU name.
+// The 2D stage kernel's blocks sweep row chunks of a band.  The tile shape trades redundant
+// work against balance: taller chunks waste fewer ring rows, narrower bands more ring
+// columns and lanes, while the tile count sets how evenly the blocks fill the SMs.  The
+// autotuner times one stage launch of a problem for each candidate shape (chunk height x
+// band count) on a scratch copy of the caller's moments, keeps the fastest in a process-wide
+// table keyed by (equation, characteristic decomposition, precision, grid), and the table is
+// consulted by every later single-solve launch of such a problem (the batched launches size
+// their work items from the load instead).  The table can be saved and loaded as text;
+// entries carry the GPU name.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -23,17 +26,17 @@ namespace hw {
 
 using TuneKey = std::tuple<int, int, int, int, int>;
 static std::mutex g_tune_mu;
-static std::map<TuneKey, int> g_tune;
+static std::map<TuneKey, TileShape> g_tune;
 
-int tuning_rows(int eq, int characteristic, int mixed, int nx, int ny) {
+TileShape tuning_shape(int eq, int characteristic, int mixed, int nx, int ny) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(TuneKey(eq, characteristic, mixed, nx, ny));
-  return it == g_tune.end() ? 0 : it->second;
+  return it == g_tune.end() ? TileShape() : it->second;
 }
 
-void tuning_set_rows(int eq, int characteristic, int mixed, int nx, int ny, int rows) {
+void tuning_set_shape(int eq, int characteristic, int mixed, int nx, int ny, TileShape t) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[TuneKey(eq, characteristic, mixed, nx, ny)] = rows;
+  g_tune[TuneKey(eq, characteristic, mixed, nx, ny)] = t;
 }
 
 static std::string device_name() {
@@ -59,7 +62,7 @@ using namespace hw;
 extern "C" {
 
 int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, int* best_rows,
-                   double* best_ms) {
+                   int* best_bands, double* best_ms) {
   if (!e || !p || !host) return HWENO_ERR_ARG;
   if (p->dim != 2) {
     engine_set_error(e, "the autotuner covers 2D problems");
@@ -76,38 +79,51 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
     engine_release_solve(e, s);
     return rc;
   }
-  const int cand[] = {0, 8, 16, 32, 64, 128, 256};
+  // candidates: chunk heights (0 = one wave over the resident slots) x band counts (0 = the
+  // widest bands of at most 126 columns; then 1.25, 1.5 and 2 times as many)
+  const int rows_c[] = {0, 8, 16, 32, 64, 128, 256};
+  const int bmin = (p->nx + 125) / 126;
+  int bands_c[4] = {0, (5 * bmin + 3) / 4, (3 * bmin + 1) / 2, 2 * bmin};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  int best = 0;
+  TileShape best;
   float best_t = 1e30f;
   const KStage S = solve_stage(s, 1);
   const KProblem kp = solve_kproblem(s);
-  for (int r : cand) {
-    if (r > 0 && r >= p->ny && r != cand[1]) continue;
-    tuning_force_rows(r > 0 ? r : -1);  // -1: the default geometry, ignoring the table
-    float tmin = 1e30f;
-    for (int rep = 0; rep < 4; ++rep) {
-      cudaEventRecord(a, st);
-      cudaError_t c = launch_stage2d(p->equation, p->equation == HWENO_EULER && p->characteristic,
-                                     p->precision == HWENO_MIXED32, kp, S, st);
-      cudaEventRecord(b, st);
-      if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
-        rc = HWENO_ERR_CUDA;
-        break;
+  for (int bi = 0; bi < 4 && rc == HWENO_OK; ++bi) {
+    const int bc = bands_c[bi];
+    if (bi > 0 && (bc <= bmin || bc > p->nx || bc == bands_c[bi - 1])) continue;
+    for (int r : rows_c) {
+      if (r > 0 && r >= p->ny && r != rows_c[1]) continue;
+      TileShape t;
+      t.rows = r > 0 ? r : -1;
+      t.bands = bc > 0 ? bc : -1;
+      tuning_force_shape(t);
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a, st);
+        cudaError_t c = launch_stage2d(p->equation,
+                                       p->equation == HWENO_EULER && p->characteristic,
+                                       p->precision == HWENO_MIXED32, kp, S, st);
+        cudaEventRecord(b, st);
+        if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+          rc = HWENO_ERR_CUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < tmin) tmin = ms;
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      if (rep > 0 && ms < tmin) tmin = ms;
-    }
-    if (rc) break;
-    if (tmin < best_t) {
-      best_t = tmin;
-      best = r;
+      if (rc) break;
+      if (tmin < best_t) {
+        best_t = tmin;
+        best.rows = r;
+        best.bands = bc;
+      }
     }
   }
-  tuning_force_rows(0);
+  tuning_force_shape(TileShape());
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   engine_release_solve(e, s);
@@ -115,9 +131,13 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
     engine_set_error(e, "autotune launch failed");
     return rc;
   }
-  tuning_set_rows(p->equation, p->equation == HWENO_EULER ? p->characteristic : 0,
-                  p->precision == HWENO_MIXED32, p->nx, p->ny, best > 0 ? best : -1);
-  if (best_rows) *best_rows = best;
+  TileShape keep;
+  keep.rows = best.rows > 0 ? best.rows : -1;
+  keep.bands = best.bands > 0 ? best.bands : -1;
+  tuning_set_shape(p->equation, p->equation == HWENO_EULER ? p->characteristic : 0,
+                   p->precision == HWENO_MIXED32, p->nx, p->ny, keep);
+  if (best_rows) *best_rows = best.rows;
+  if (best_bands) *best_bands = best.bands;
   if (best_ms) *best_ms = best_t;
   return HWENO_OK;
 }
@@ -128,11 +148,11 @@ int hweno_tuning_save(const char* path) {
   if (!f) return HWENO_ERR_ARG;
   const std::string dev = device_name();
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  std::fprintf(f, "# hweno tuning table: gpu equation characteristic mixed nx ny rows\n");
+  std::fprintf(f, "# hweno tuning table: gpu equation characteristic mixed nx ny rows bands\n");
   for (auto& kv : g_tune)
-    std::fprintf(f, "%s %d %d %d %d %d %d\n", dev.c_str(), std::get<0>(kv.first),
+    std::fprintf(f, "%s %d %d %d %d %d %d %d\n", dev.c_str(), std::get<0>(kv.first),
                  std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
-                 std::get<4>(kv.first), kv.second);
+                 std::get<4>(kv.first), kv.second.rows, kv.second.bands);
   std::fclose(f);
   return HWENO_OK;
 }
@@ -146,10 +166,12 @@ int hweno_tuning_load(const char* path) {
   int n = 0;
   while (std::fgets(line, sizeof line, f)) {
     if (line[0] == '#') continue;
-    int eq, ch, mx, nx, ny, rows;
-    if (std::sscanf(line, "%255s %d %d %d %d %d %d", name, &eq, &ch, &mx, &nx, &ny, &rows) == 7 &&
+    int eq, ch, mx, nx, ny;
+    TileShape t;
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d", name, &eq, &ch, &mx, &nx, &ny, &t.rows,
+                    &t.bands) == 8 &&
         dev == name) {
-      tuning_set_rows(eq, ch, mx, nx, ny, rows);
+      tuning_set_shape(eq, ch, mx, nx, ny, t);
       ++n;
     }
   }
