@@ -79,7 +79,10 @@ def _workload_config(n, extra=None):
     cfg = {"workload": f"2D Euler quadrant+vortex {n}x{n}, 3 moments x 4 components, "
                        f"transmissive, CFL 0.6, SSP-RK3 step = 3 fused stages",
            "cells": n * n, "global_batch": 1, "seq_len": n * n, "parallelism": "replicas",
-           "l2": "inputs larger than L2 (state 402 MB per buffer), no flush"}
+           "l2": (f"inputs larger than L2 (state {n * n * 96 / 1e6:.0f} MB per buffer), no flush"
+                  if n * n * 96 > 129e6 else
+                  f"state {n * n * 96 / 1e6:.0f} MB per buffer fits in L2; no flush (the stage "
+                  f"kernel is FP64-bound, not memory-bound)")}
     if extra:
         cfg.update(extra)
     return cfg
