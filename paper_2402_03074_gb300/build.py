@@ -3,6 +3,7 @@ into a shared library with the C ABI of include/hweno.h."""
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import subprocess
 import sys
@@ -14,7 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhweno.so")
 SOURCES = ["stage1d.cu", "stage2d.cu", "batch.cu", "engine.cu", "server.cu", "tune.cu",
            "static_batch.cu"]
-HEADERS = ["hweno_device.cuh", "launch.h", "server.h", "batch.h", "stage2d_item.cuh"]
+HEADERS = ["hweno_device.cuh", "launch.h", "server.h", "batch.h", "stage1d_item.cuh",
+           "stage2d_item.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-I" + os.path.join(ROOT, "include")]
@@ -33,7 +35,18 @@ def _stale(target: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile what is out of date.  Processes that build at the same time (one per rank of a
+    multi-GPU launch) take turns on a lock file; the later ones find everything current."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            return _build(force, verbose)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build(force: bool, verbose: bool) -> str:
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "hweno.h")]
     jobs = []
     objs = []
