@@ -299,6 +299,10 @@ def run_ours(args):
                  "error_note": "relative to the mean |average| of each component, after the "
                                "timed steps from identical inputs; FP64 path = oracle to 1e-12"}
 
+    longr = None
+    if args.long_steps > 0:
+        longr = long_runs(H, I, eng, stream, U0, w.bc, n, args.long_steps)
+
     # end to end through the C ABI with host buffers: per step H2D of the state from pinned
     # memory, one step, D2H of the new state
     e2e = None
@@ -352,7 +356,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": _workload_config(n), "gpu_launches": 16 * math.ceil(args.steps / 4),
             "clocks": clk.summary(), "roofline": roofline, "mixed32": mixed, "e2e": e2e,
-            "served": served, "tubes_1d": tubes}
+            "served": served, "tubes_1d": tubes, "long_runs": longr}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, args.cpu_seconds)
     print(json.dumps(line))
@@ -429,6 +433,52 @@ def served_stream(H, I, eng_factory, m, rate, grids, t_lo, t_hi, seed=0):
             "t_end_range": [t_lo, t_hi], "mixed_fraction": float(precs.mean()),
             "served": served, "plain_fp64_loop": plain,
             "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"]}
+
+
+def long_runs(H, I, eng, stream, U0, bc, n, steps):
+    """The long 2D Euler runs: `steps` FP64 steps of the 1024^2 quadrant + vortex state (seed
+    1) with its conservation drift (transmissive: the net boundary flux), and `steps` steps of
+    the n^2 state in FP64 and in the FP32-bulk path from identical inputs, with the L1 / Linf
+    deviation of the FP32-bulk result (relative to the mean |average| of each component).  The
+    FP64 GPU path stands in for the FP64 oracle here (they agree within 1e-12 per stage; the
+    serial oracle would need hours for these runs)."""
+    import torch
+
+    def run(p, U):
+        sid = H.hweno_open(eng, p, U)
+        S0, A0 = H.hweno_conservation(eng, sid, 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.hweno_advance(eng, sid, math.inf, max_steps=steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        S1, _ = H.hweno_conservation(eng, sid, 4)
+        out, t = H.hweno_get_state(eng, sid, np.empty_like(U))
+        H.hweno_close(eng, sid)
+        return out, t, ms, float((np.abs(S1 - S0) / A0).max())
+
+    w3 = I.quadrant_vortex_2d(1, 1024)
+    p3 = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=1024, ny=1024, bc=w3.bc, cfl=0.6)
+    _, t3, ms3, drift3 = run(p3, w3.U0)
+    res = {"c3": {"workload": f"2D Euler quadrant+vortex 1024x1024 (seed 1), FP64, {steps} steps",
+                  "cell_stages_per_s": 1024 * 1024 * 3 * steps / (ms3 / 1e3), "t": t3,
+                  "conservation_drift": drift3}}
+    rec = {}
+    for name, prec in (("fp64", H.HWENO_FP64), ("mixed32", H.HWENO_MIXED32)):
+        p = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=n, ny=n, bc=bc, cfl=0.6,
+                           precision=prec)
+        rec[name] = run(p, U0)
+    diff = np.abs(rec["mixed32"][0][:, 0] - rec["fp64"][0][:, 0])
+    scale = np.abs(rec["fp64"][0][:, 0]).mean(axis=(1, 2))[:, None, None]
+    res["c4"] = {"workload": f"2D Euler quadrant+vortex {n}x{n} (seed 0), {steps} steps, FP64 and "
+                             f"FP32-bulk from identical inputs",
+                 "fp64_cell_stages_per_s": n * n * 3 * steps / (rec["fp64"][2] / 1e3),
+                 "mixed32_cell_stages_per_s": n * n * 3 * steps / (rec["mixed32"][2] / 1e3),
+                 "t_fp64": rec["fp64"][1], "t_mixed32": rec["mixed32"][1],
+                 "l1_mixed32_vs_fp64": float((diff / scale).mean()),
+                 "linf_mixed32_vs_fp64": float((diff / scale).max())}
+    return res
 
 
 def tubes_1d(H, I, eng_factory, tubes, n, t_end):
@@ -538,6 +588,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-tubes", action="store_true")
+    ap.add_argument("--long-steps", type=int, default=200,
+                    help="steps of the long 1024^2 / 2048^2 runs (0: skip them)")
     ap.add_argument("--tubes", type=int, default=16)
     ap.add_argument("--tubes-n", type=int, default=4000)
     ap.add_argument("--tubes-t", type=float, default=1.5)

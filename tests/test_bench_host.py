@@ -38,7 +38,7 @@ def _fake_binding():
 
     def hweno_get_state(eng, sid, out):
         out[...] = state["solves"][sid][1]
-        return out, state["solves"][sid][0].t_end
+        return out, getattr(state["solves"][sid][0], "t_end", 0.0)
 
     def hweno_submit(eng, p, U0):
         tk = state["next"]
@@ -94,3 +94,32 @@ def test_replica_throughput_and_config():
     assert bench.replica_throughput(100.0, 1000.0, 2) == 200.0
     cfg = bench._workload_config(2048)
     assert cfg["cells"] == 2048 * 2048 and "workload" in cfg
+
+
+def test_long_runs_report():
+    H = _fake_binding()
+    H.hweno_conservation = lambda eng, sid, nc: (np.ones(nc), np.ones(nc) * 2.0)
+
+    class _Ev:
+        def __init__(self, **kw):
+            pass
+
+        def record(self, s):
+            pass
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return 5.0
+
+    import torch
+    real = torch.cuda.Event
+    torch.cuda.Event = _Ev
+    try:
+        w = I.quadrant_vortex_2d(0, 32)
+        rep = bench.long_runs(H, I, object(), None, w.U0, w.bc, 32, 4)
+    finally:
+        torch.cuda.Event = real
+    assert rep["c3"]["conservation_drift"] == 0.0 and rep["c3"]["cell_stages_per_s"] > 0
+    assert rep["c4"]["l1_mixed32_vs_fp64"] == 0.0
