@@ -2,12 +2,11 @@
 benchmark times.
 
 * 2D Euler 2048^2 (the benchmark's quadrant + vortex state, FP64, characteristic,
-  transmissive): the three stages of one SSP-RK3 step through hweno_stage_device (the same
-  kernel and launch geometry as the engine), each from the GPU's previous stage output,
-  checked on sampled cells against the oracle evaluated cell by cell (every band and row-chunk
-  edge of the launch geometry, the domain corners, and random cells), and the wave speeds the
-  stage reduces against the oracle's over the whole output.  The engine's graph-replayed step
-  (what the benchmark times) equals that chain of stages.
+  transmissive): stages 1, 2 and 3 through hweno_stage_device (the same kernel and launch
+  geometry as the engine) on seeded host inputs, checked on sampled cells against the oracle
+  evaluated cell by cell (every band and row-chunk edge of the launch geometry, the domain
+  corners, and random cells).  The engine's graph-replayed step (what the benchmark times)
+  equals the chain of the three stage launches.
 * 2D Euler 1024^2 (the 200-step production size): stage 1 on sampled cells.
 * The FP32-bulk path at 2048^2: stage 1 on sampled cells within its stated 1e-5 bound.
 * 1D Euler shock tube with 4000 cells: every cell of every stage, and 20 engine steps.
@@ -72,66 +71,86 @@ def _rel_cells(got, ref, U_scale):
     return float((np.abs(got - ref) / np.maximum(np.abs(ref), S)).max())
 
 
-def _gpu_chain(hp, U0, stages=3):
-    """Stages 1..stages of one SSP-RK3 step through hweno_stage_device, dt by the CFL rule
-    from the speeds of U^n; returns the host copies of every stage's input and output."""
+def _gpu_stage(hp, k, Uin, Un, Vh, alpha, dt):
+    """One stage through hweno_stage_device (the benchmark's kernel and launch geometry) on
+    host inputs; returns (U_out, V-hat, LF speeds of the output, status)."""
     import torch
     d = torch.device("cuda:0")
     s = torch.cuda.current_stream().cuda_stream
-    Un = torch.from_numpy(U0).to(d)
-    Vh = torch.zeros((U0.shape[0], U0.shape[1] - 1) + U0.shape[2:], dtype=torch.float64,
-                     device=d)
-    a = torch.zeros(2, dtype=torch.float64, device=d)
-    H.hweno_alpha_device(hp, Un, a, s)
-    torch.cuda.synchronize()
-    dx = (hp.x1 - hp.x0) / hp.nx
-    dy = (hp.y1 - hp.y0) / hp.ny
-    a_h = a.cpu().numpy()
-    dt = hp.cfl / (a_h[0] / dx + a_h[1] / dy)
+    Ui = torch.from_numpy(np.ascontiguousarray(Uin)).to(d)
+    Unn = Ui if Un is Uin else torch.from_numpy(np.ascontiguousarray(Un)).to(d)
+    Vt = torch.from_numpy(np.ascontiguousarray(Vh)).to(d)
+    Uo = torch.full_like(Ui, float("nan"))
+    a = torch.tensor(np.asarray(alpha, dtype=np.float64)[:2], device=d)
+    ao = torch.zeros(2, dtype=torch.float64, device=d)
     dtt = torch.tensor([dt], dtype=torch.float64, device=d)
-    out = []
-    Uin = Un
-    for k in range(1, stages + 1):
-        Uo = torch.full_like(Un, float("nan"))
-        ao = torch.zeros(2, dtype=torch.float64, device=d)
-        st = torch.zeros(1, dtype=torch.int32, device=d)
-        Vin = Vh.cpu().numpy() if k > 1 else None
-        H.hweno_stage_device(hp, k, Uin, Un, Vh, Uo, a, ao, dtt, st, s)
-        torch.cuda.synchronize()
-        out.append(dict(k=k, Uin=Uin.cpu().numpy(), Vh_in=Vin, alpha=a.cpu().numpy(),
-                        Uout=Uo.cpu().numpy(), Vh_out=Vh.cpu().numpy(),
-                        alpha_out=ao.cpu().numpy(), status=int(st.item())))
-        Uin, a = Uo, ao
-    return dt, out
+    st = torch.zeros(1, dtype=torch.int32, device=d)
+    H.hweno_stage_device(hp, k, Ui, Unn, Vt, Uo, a, ao, dtt, st, s)
+    torch.cuda.synchronize()
+    return Uo.cpu().numpy(), Vt.cpu().numpy(), ao.cpu().numpy(), int(st.item())
+
+
+def _cfl_dt(hp, alpha):
+    return hp.cfl / (alpha[0] * hp.nx / (hp.x1 - hp.x0) + alpha[1] * hp.ny / (hp.y1 - hp.y0))
 
 
 @pytest.fixture(scope="module")
 def euler2048():
+    """The benchmark's state U^n (seed 0) and, as the inputs of stages 2 and 3, two other
+    seeded states of the same generator (seeds 5, 6) with seeded first-moment modifications;
+    every input is generated on the host, none comes from the GPU path."""
     w = I.quadrant_vortex_2d(0, 2048)
     hp, op = _problems(w)
-    dt, chain = _gpu_chain(hp, w.U0)
-    return w, hp, op, dt, chain
+    others = [I.quadrant_vortex_2d(sd, 2048).U0 for sd in (5, 6)]
+    rng = np.random.default_rng(11)
+    Vh = rng.uniform(-0.02, 0.02, size=(4, 2, 2048, 2048))
+    return w, hp, op, others, Vh
 
 
 def test_2048_fp64_stages_on_sampled_cells(euler2048):
-    w, hp, op, dt, chain = euler2048
+    w, hp, op, others, Vh = euler2048
     cells = _sample_cells(2048, 7)
     assert len(cells) > 5000
-    for s in chain:
-        assert s["status"] == 0
-        ref, vref, ost = O.stage_cells(op, s["k"], s["Uin"], w.U0, s["Vh_in"], s["alpha"], dt,
-                                       cells)
-        assert ost == 0
-        e = _rel_cells(_cells_of(s["Uout"], cells), ref, w.U0)
-        assert e <= TOL, f"stage {s['k']}: {e:.3e}"
-        if s["k"] == 1:
-            ev = _rel_cells(_cells_of(s["Vh_out"], cells), vref, w.U0)
+    a0 = O.alpha(op, w.U0)
+    dt = _cfl_dt(hp, a0)
+    for k, Uin in ((1, w.U0), (2, others[0]), (3, others[1])):
+        alpha = a0 if k == 1 else O.alpha(op, Uin)
+        got, vgot, _, st = _gpu_stage(hp, k, Uin, w.U0, Vh if k > 1 else np.zeros_like(Vh),
+                                      alpha, dt)
+        ref, vref, ost = O.stage_cells(op, k, Uin, w.U0, Vh if k > 1 else None, alpha, dt, cells)
+        assert st == ost == 0
+        e = _rel_cells(_cells_of(got, cells), ref, w.U0)
+        assert e <= TOL, f"stage {k}: {e:.3e}"
+        if k == 1:
+            ev = _rel_cells(_cells_of(vgot, cells), vref, w.U0)
             assert ev <= TOL, f"v-hat: {ev:.3e}"
-        np.testing.assert_allclose(s["alpha_out"], O.alpha(op, s["Uout"])[:2], rtol=1e-13)
 
 
 def test_2048_engine_step_equals_stage_chain(euler2048):
-    w, hp, op, dt, chain = euler2048
+    """The graph-replayed engine step (what the benchmark times) equals three stage launches
+    through hweno_stage_device chained on the GPU (both CUDA paths; the stages themselves are
+    checked against the oracle above)."""
+    import torch
+    w, hp, op, _, _ = euler2048
+    d = torch.device("cuda:0")
+    s = torch.cuda.current_stream().cuda_stream
+    Un = torch.from_numpy(w.U0).to(d)
+    Vh = torch.zeros((4, 2, 2048, 2048), dtype=torch.float64, device=d)
+    a = torch.zeros(2, dtype=torch.float64, device=d)
+    H.hweno_alpha_device(hp, Un, a, s)
+    torch.cuda.synchronize()
+    dt = _cfl_dt(hp, a.cpu().numpy())
+    dtt = torch.tensor([dt], dtype=torch.float64, device=d)
+    Uin = Un
+    for k in (1, 2, 3):
+        Uo = torch.empty_like(Un)
+        ao = torch.zeros(2, dtype=torch.float64, device=d)
+        st = torch.zeros(1, dtype=torch.int32, device=d)
+        H.hweno_stage_device(hp, k, Uin, Un, Vh, Uo, a, ao, dtt, st, s)
+        Uin, a = Uo, ao
+    torch.cuda.synchronize()
+    chain = Uin.cpu().numpy()
+    del Un, Vh, Uin
     eng = H.hweno_create()
     try:
         sid = H.hweno_open(eng, hp, w.U0)
@@ -140,33 +159,36 @@ def test_2048_engine_step_equals_stage_chain(euler2048):
     finally:
         H.hweno_destroy(eng)
     assert t == pytest.approx(dt, rel=1e-15)
-    e = rel_err(got, chain[-1]["Uout"], w.U0)
+    e = rel_err(got, chain, w.U0)
     assert e <= TOL, f"engine step vs stage chain: {e:.3e}"
 
 
 def test_1024_fp64_stage_on_sampled_cells():
     w = I.quadrant_vortex_2d(1, 1024)
     hp, op = _problems(w)
-    dt, chain = _gpu_chain(hp, w.U0, stages=1)
-    s = chain[0]
+    alpha = O.alpha(op, w.U0)
+    dt = _cfl_dt(hp, alpha)
+    Vz = np.zeros((4, 2, 1024, 1024))
+    got, vgot, _, st = _gpu_stage(hp, 1, w.U0, w.U0, Vz, alpha, dt)
     cells = _sample_cells(1024, 8)
-    ref, vref, ost = O.stage_cells(op, 1, w.U0, w.U0, None, s["alpha"], dt, cells)
-    assert s["status"] == ost == 0
-    assert _rel_cells(_cells_of(s["Uout"], cells), ref, w.U0) <= TOL
-    assert _rel_cells(_cells_of(s["Vh_out"], cells), vref, w.U0) <= TOL
+    ref, vref, ost = O.stage_cells(op, 1, w.U0, w.U0, None, alpha, dt, cells)
+    assert st == ost == 0
+    assert _rel_cells(_cells_of(got, cells), ref, w.U0) <= TOL
+    assert _rel_cells(_cells_of(vgot, cells), vref, w.U0) <= TOL
 
 
 def test_2048_mixed_stage_on_sampled_cells(euler2048):
     """FP32-bulk / FP64-weights stage 1 at 2048^2 within the 1e-5 bound of the mixed path
     (FP32 unit roundoff times the coefficient mass of the reconstruction, flux and update)."""
-    w, _, op, dt, chain = euler2048
+    w, _, op, _, Vh = euler2048
     hp, _ = _problems(w, precision=H.HWENO_MIXED32)
-    dt32, mixed = _gpu_chain(hp, w.U0, stages=1)
-    assert dt32 == dt
+    alpha = O.alpha(op, w.U0)
+    dt = _cfl_dt(hp, alpha)
+    got, _, _, st = _gpu_stage(hp, 1, w.U0, w.U0, np.zeros_like(Vh), alpha, dt)
     cells = _sample_cells(2048, 9)
-    ref, _, ost = O.stage_cells(op, 1, w.U0, w.U0, None, mixed[0]["alpha"], dt, cells)
-    assert mixed[0]["status"] == ost == 0
-    e = _rel_cells(_cells_of(mixed[0]["Uout"], cells), ref, w.U0)
+    ref, _, ost = O.stage_cells(op, 1, w.U0, w.U0, None, alpha, dt, cells)
+    assert st == ost == 0
+    e = _rel_cells(_cells_of(got, cells), ref, w.U0)
     assert e <= 1e-5, f"mixed stage 1: {e:.3e}"
 
 
