@@ -531,6 +531,46 @@ def tubes_1d(H, I, eng_factory, tubes, n, t_end):
             "same_steps": steps_b == steps}
 
 
+def run_paper_tables(args):
+    """The paper's accuracy examples at their finest mesh (240 cells per direction) to their end
+    times at CFL 0.6, FP64: GPU wall time per run (host clock, state upload to result
+    download) and L1 / Linf error of the cell averages against the exact solution, next to
+    the paper's serial CPU time of the same mesh (Tables 3.1, 3.3, 3.4, 3.6; context only: the
+    paper does not state its time step or time unit)."""
+    import torch
+    from paper_2402_03074_gb300 import build as B
+    B.build()
+    from paper_2402_03074_gb300 import _binding as H
+    from paper_2402_03074_gb300 import inputs as I
+    n = 240
+    cases = [
+        ("Table 3.1, 1D Burgers", I.burgers_sine_1d(n), H.HWENO_BURGERS,
+         lambda t: I.burgers_exact_1d(n, t), 1.56e-01),
+        ("Table 3.3, 1D Euler", I.euler_density_wave_1d(n), H.HWENO_EULER,
+         lambda t: I.euler_density_wave_exact_1d(n, t), 1.34e01),
+        ("Table 3.4, 2D Burgers", I.burgers_sine_2d(n), H.HWENO_BURGERS,
+         lambda t: I.burgers_exact_2d(n, t), 3.69e02),
+        ("Table 3.6, 2D Euler", I.euler_density_wave_2d(n), H.HWENO_EULER,
+         lambda t: I.euler_density_wave_exact_2d(n, t), 2.14e05),
+    ]
+    eng = H.hweno_create()
+    for name, w, eq, exact, paper_s in cases:
+        p = H.make_problem(dim=w.dim, equation=eq, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1,
+                           y0=w.y0, y1=w.y1, bc=w.bc, cfl=0.6)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sid = H.hweno_open(eng, p, w.U0)
+        steps = H.hweno_advance(eng, sid, w.t_end)
+        out, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        el = time.perf_counter() - t0
+        H.hweno_close(eng, sid)
+        e = np.abs(out[0, 0] - exact(w.t_end)[0, 0])
+        print(json.dumps({"case": name, "mesh": n, "t_end": w.t_end, "steps": steps,
+                          "gpu_seconds": el, "l1": float(e.mean()), "linf": float(e.max()),
+                          "paper_cpu_time": paper_s}), flush=True)
+    H.hweno_destroy(eng)
+
+
 def run_sweep(args):
     """Convergence of the FP64 and FP32-bulk paths on the periodic isentropic vortex
     (rho = p = 1, u = v = 1 plus the vortex, [0,1]^2, T = 0.05) against the exact translated
@@ -598,6 +638,8 @@ def main():
     ap.add_argument("--served-tlo", type=float, default=0.02)
     ap.add_argument("--served-thi", type=float, default=0.05)
     ap.add_argument("--sweep", action="store_true", help="precision / convergence study")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="the paper's accuracy examples at 240 cells per direction")
     ap.add_argument("--sweep-sizes", default="128,256,512,1024,2048")
     ap.add_argument("--sweep-T", type=float, default=0.05)
     args = ap.parse_args()

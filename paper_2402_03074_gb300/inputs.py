@@ -225,6 +225,15 @@ def burgers_sine_2d(n: int, t_end: float = 0.5 / math.pi) -> Workload:
                     t_end, moments_2d(f, 0.0, 4.0, 0.0, 4.0, n, n))
 
 
+def burgers_exact_2d(n: int, t: float) -> np.ndarray:
+    """Exact moments of the 2D Burgers example before the shock: u depends on s = x + y only,
+    u_t + 2 u u_s = 0, so u = u0(s - 2 u t) (the 1D characteristic relation at time 2t)."""
+    u0 = lambda s: 0.5 + np.sin(np.pi * s / 2.0)
+    du0 = lambda s: 0.5 * np.pi * np.cos(np.pi * s / 2.0)
+    return moments_2d(lambda x, y: _burgers_exact_points(x + y, 2.0 * t, u0, du0), 0.0, 4.0,
+                      0.0, 4.0, n, n)
+
+
 def advection_sine_2d(n: int, t_end: float = 1.0, ax: float = 1.0, ay: float = 1.0) -> Workload:
     f = lambda x, y: 0.5 + np.sin(np.pi * (x + y) / 2.0)
     return Workload("advection_sine_2d", 2, ADVECTION, n, n, 0.0, 4.0, 0.0, 4.0,

@@ -252,3 +252,26 @@ def test_lax_problem_scale_invariance_of_the_weights():
         dev[wm] = np.abs(res[2.0 ** 20] - res[1.0]).max() / np.abs(res[1.0]).max()
     assert dev[O.W_SCALE_INVARIANT] < 4e-3
     assert dev[O.W_ORIGINAL] > 10 * dev[O.W_SCALE_INVARIANT]
+
+
+def test_2d_burgers_converges_to_the_characteristic_solution():
+    """Example 3.3 (2D Burgers, u0 = 0.5 + sin(pi (x + y) / 2) on (0,4)^2, before the shock)
+    against the exact solution u = u0(x + y - 2 u t), dt ~ dx^(5/3): with the linear weights
+    fifth order (order > 4.5 from 32^2 to 64^2); with the scale-invariant weights the error
+    falls faster than third order there (still pre-asymptotic at these meshes; the paper's
+    Table 3.4 reaches fifth order from 120^2 on)."""
+    T = 0.1
+    errs = {O.W_LINEAR: [], O.W_SCALE_INVARIANT: []}
+    for n in (32, 64):
+        w = I.burgers_sine_2d(n, t_end=T)
+        ex = I.burgers_exact_2d(n, T)[0, 0]
+        for wm in errs:
+            P = O.Problem(dim=2, eq=O.BURGERS, nx=n, ny=n, x0=0.0, x1=4.0, y0=0.0, y1=4.0,
+                          weights=wm)
+            U, t, _, st = O.run(P, w.U0, 0.0, T,
+                                dt_fixed=0.02 * 4.0 / n * (16.0 / n) ** (2.0 / 3.0))
+            assert st == 0 and t == T
+            errs[wm].append(np.abs(U[0, 0] - ex).mean())
+    lin, si = errs[O.W_LINEAR], errs[O.W_SCALE_INVARIANT]
+    assert math.log(lin[0] / lin[1], 2) > 4.5, lin
+    assert math.log(si[0] / si[1], 2) > 3.0, si
