@@ -328,7 +328,9 @@ def run_ours(args):
 
     served = None
     if not args.no_served:
-        served = served_stream(H, I, lambda: H.hweno_create(device=dev), args.served_m, 50.0,
+        budget = 150 * 10**9  # the served configuration's HBM admission budget
+        served = served_stream(H, I, lambda: H.hweno_create(device=dev, hbm_budget_bytes=budget),
+                               args.served_m, 50.0,
                                [int(g) for g in args.served_grids.split(",")],
                                args.served_tlo, args.served_thi, seed=rank)
     tubes = None
@@ -430,6 +432,7 @@ def served_stream(H, I, eng_factory, m, rate, grids, t_lo, t_hi, seed=0):
     H.hweno_destroy(eng)
     plain = stats(fin, t0)
     return {"requests": m, "rate_per_s": rate, "grids": [int(g) for g in grids],
+            "hbm_budget_bytes": 150 * 10**9,
             "t_end_range": [t_lo, t_hi], "mixed_fraction": float(precs.mean()),
             "served": served, "plain_fp64_loop": plain,
             "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"]}
@@ -647,6 +650,8 @@ def main():
         args.warmup = 3
     if args.sweep:
         run_sweep(args)
+    elif args.paper_tables:
+        run_paper_tables(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
