@@ -216,6 +216,53 @@ def lax_1d(n: int = 100, zeta: float = 1.0) -> Workload:
                       (0.5 * zeta, 0.0, 0.571 * zeta), -0.5, 0.5, 0.0, n, 0.16)
 
 
+def blast_wave_1d(n: int = 800) -> Workload:
+    """Example 3.6: interacting blast waves on [0, 1], reflective walls, T = 0.038; pressure
+    1000 / 0.01 / 100 with jumps at x = 0.1 and 0.9 (faces for n a multiple of 10)."""
+    def f(x):
+        p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+        return euler_conserved(np.ones_like(x), np.zeros_like(x), p)
+    return Workload("blast_wave_1d", 1, EULER, n, 1, 0.0, 1.0, 0.0, 1.0, (BC_REFLECTIVE,) * 4,
+                    0.038, moments_1d(f, 0.0, 1.0, n))
+
+
+def shu_osher_1d(n: int = 400) -> Workload:
+    """Example 3.7: a Mach-3 shock running into the entropy wave rho = 1 + 0.2 sin(5x) on
+    [-5, 5], outflow (transmissive) boundaries, T = 1.8; the jump at x = -4 is a face for n a
+    multiple of 10."""
+    def f(x):
+        left = x < -4.0
+        rho = np.where(left, 3.857143, 1.0 + 0.2 * np.sin(5.0 * x))
+        return euler_conserved(rho, np.where(left, 2.629369, 0.0), np.where(left, 10.333333, 1.0))
+    return Workload("shu_osher_1d", 1, EULER, n, 1, -5.0, 5.0, 0.0, 1.0, (BC_TRANSMISSIVE,) * 4,
+                    1.8, moments_1d(f, -5.0, 5.0, n))
+
+
+def double_rarefaction_1d(n: int = 400) -> Workload:
+    """Example 3.8: double rarefaction (rho = 7, p = 0.2, u = -1 / +1 at x = 0) on [-1, 1],
+    outflow boundaries, T = 0.6: a near-vacuum forms at the centre."""
+    return riemann_1d("double_rarefaction_1d", (7.0, -1.0, 0.2), (7.0, 1.0, 0.2), -1.0, 1.0, 0.0,
+                      n, 0.6)
+
+
+def sedov_1d(n: int = 800) -> Workload:
+    """Example 3.9: Sedov blast wave on [-2, 2], rho = 1, u = 0, E = 1e-12 except the centre
+    cell with E = 3200000 / dx; outflow boundaries, T = 0.001.  For even n the centre x = 0 is
+    a face: the energy 3200000 is then split equally between the two cells at the centre
+    (the reading taken for the paper's 800 cells)."""
+    dx = 4.0 / n
+    E = np.full(n, 1e-12)
+    if n % 2:
+        E[n // 2] = 3200000.0 / dx
+    else:
+        E[n // 2 - 1] = E[n // 2] = 0.5 * 3200000.0 / dx
+    U = np.zeros((3, 2, 1, n))
+    U[0, 0, 0, :] = 1.0
+    U[2, 0, 0, :] = E
+    return Workload("sedov_1d", 1, EULER, n, 1, -2.0, 2.0, 0.0, 1.0, (BC_TRANSMISSIVE,) * 4,
+                    0.001, U)
+
+
 # ------------------------------------------------------------------------------------------
 # 2D workloads
 # ------------------------------------------------------------------------------------------

@@ -275,3 +275,49 @@ def test_2d_burgers_converges_to_the_characteristic_solution():
     lin, si = errs[O.W_LINEAR], errs[O.W_SCALE_INVARIANT]
     assert math.log(lin[0] / lin[1], 2) > 4.5, lin
     assert math.log(si[0] / si[1], 2) > 3.0, si
+
+
+def _run_example(w):
+    P = O.Problem(dim=1, eq=O.EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
+    U, t, ns, st = O.run(P, w.U0, 0.0, w.t_end)
+    return U, t, ns, st
+
+
+def test_shock_examples_run_without_positivity_limiter():
+    """Examples 3.6-3.9 at the paper's meshes: the scheme runs to the end time with positive
+    density and pressure and no positivity-preserving limiter (the paper says so for the
+    double rarefaction and the Sedov problem, Examples 3.8-3.9)."""
+    for gen in (I.blast_wave_1d, I.shu_osher_1d, I.double_rarefaction_1d, I.sedov_1d):
+        w = gen()
+        U, t, ns, st = _run_example(w)
+        assert st == 0 and t == w.t_end, w.name
+        rho, m, E = U[0, 0, 0], U[1, 0, 0], U[2, 0, 0]
+        assert (rho > 0).all() and (E - 0.5 * m * m / rho > 0).all(), w.name
+
+
+def test_blast_wave_conserves_mass_and_energy_between_reflective_walls():
+    """Example 3.6: no mass or energy crosses a reflective wall (the wall flux of the mirrored
+    state has zero mass and energy components), so both totals are conserved to round-off."""
+    w = I.blast_wave_1d(400)
+    U, t, ns, st = _run_example(w)
+    assert st == 0
+    for c in (0, 2):
+        s0, s1 = math.fsum(w.U0[c, 0, 0]), math.fsum(U[c, 0, 0])
+        assert abs(s1 - s0) <= 1e-13 * math.fsum(np.abs(w.U0[c, 0, 0])), (c, s1 - s0)
+
+
+def test_sedov_is_mirror_symmetric_and_conservative():
+    """Example 3.9 (energy split between the two centre cells): mass and energy are conserved
+    (the blast has not reached the boundaries at T), and the solution is symmetric about
+    x = 0 up to the amplified round-off of a 1e21 energy contrast: the FP64 evaluation is not
+    bitwise mirror-symmetric, and over the ~900 steps the shock fronts amplify that to a few
+    tenths of a percent of the peak density (at most 1 % here)."""
+    w = I.sedov_1d(400)
+    U, t, ns, st = _run_example(w)
+    assert st == 0
+    rho, m = U[0, 0, 0], U[1, 0, 0]
+    assert np.abs(rho - rho[::-1]).max() <= 1e-2 * rho.max()
+    assert np.abs(m + m[::-1]).max() <= 1e-2 * np.abs(m).max()
+    for c in (0, 2):
+        s0, s1 = math.fsum(w.U0[c, 0, 0]), math.fsum(U[c, 0, 0])
+        assert abs(s1 - s0) <= 1e-12 * math.fsum(np.abs(w.U0[c, 0, 0])), (c, s1 - s0)
