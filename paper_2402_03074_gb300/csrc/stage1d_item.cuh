@@ -20,7 +20,7 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
   const int i0 = blk * (BW - 2);
   const int i = i0 - 1 + t;  // reconstructed cell of this thread
 
-  __shared__ double win[NC * NM][BW + 2];    // moments of cells i0-2 .. i0+BW-1
+  __shared__ R win[NC * NM][BW + 2];         // moments of cells i0-2 .. i0+BW-1 (bulk precision)
   __shared__ R trL[NC][2][BW];               // left trace (u, f) of each thread's cell
   __shared__ R fhat[NC][BW + 1];             // flux at the left face of thread t's cell
   __shared__ double red[BW / 32];
@@ -33,7 +33,7 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
     const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
     double val = S.Uin[(size_t)a * nx + ii];
     if (flip) val *= mirror_sign<EQ, 1>(c, m, 1, 0);
-    win[a][col] = val;
+    win[a][col] = from_f64<R>(val);
   }
   __syncthreads();
 
@@ -44,14 +44,14 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
   if (need) {
     if constexpr (CHAR && EQ == EQ_EULER) {
       Eig1<R> E;
-      E.init(P, (R)win[0][t + 1], (R)win[2][t + 1], (R)win[4][t + 1]);
+      E.init(P, win[0][t + 1], win[2][t + 1], win[4][t + 1]);
       R Wm[3], W0[3], Wp[3], Zm[3], Zp[3];
       {
-        R Um[3] = {(R)win[0][t], (R)win[2][t], (R)win[4][t]};
-        R Uc[3] = {(R)win[0][t + 1], (R)win[2][t + 1], (R)win[4][t + 1]};
-        R Up[3] = {(R)win[0][t + 2], (R)win[2][t + 2], (R)win[4][t + 2]};
-        R Vm[3] = {(R)win[1][t], (R)win[3][t], (R)win[5][t]};
-        R Vp[3] = {(R)win[1][t + 2], (R)win[3][t + 2], (R)win[5][t + 2]};
+        R Um[3] = {win[0][t], win[2][t], win[4][t]};
+        R Uc[3] = {win[0][t + 1], win[2][t + 1], win[4][t + 1]};
+        R Up[3] = {win[0][t + 2], win[2][t + 2], win[4][t + 2]};
+        R Vm[3] = {win[1][t], win[3][t], win[5][t]};
+        R Vp[3] = {win[1][t + 2], win[3][t + 2], win[5][t + 2]};
         E.project(Um, Wm);
         E.project(Uc, W0);
         E.project(Up, Wp);
@@ -74,8 +74,8 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         R p4[4], v;
-        recon1d<R>((R)win[c * NM][t], (R)win[c * NM][t + 1], (R)win[c * NM][t + 2],
-                   (R)win[c * NM + 1][t], (R)win[c * NM + 1][t + 2], P, p4, v);
+        recon1d<R>(win[c * NM][t], win[c * NM][t + 1], win[c * NM][t + 2],
+                   win[c * NM + 1][t], win[c * NM + 1][t + 2], P, p4, v);
 #pragma unroll
         for (int g = 0; g < 4; ++g) pts[g][c] = p4[g];
         vh[c] = v;
@@ -120,8 +120,9 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
       const R F1 = -(fr - fl) * idx;
       const R vol = R(1.0 / 12.0) * (fp[0][c] + fp[3][c]) + R(5.0 / 12.0) * (fp[1][c] + fp[2][c]);
       const R F2 = (vol - R(0.5) * (fl + fr)) * idx;
-      const double own_u = win[c * NM][t + 1];
-      const double own_v = (double)vh[c];
+      const double own_u = (sizeof(R) == sizeof(double)) ? to_f64(win[c * NM][t + 1])
+                                                          : S.Uin[(size_t)(c * NM) * nx + i];
+      const double own_v = to_f64(vh[c]);
       const size_t q0 = (size_t)(c * NM) * nx + i, q1 = q0 + nx;
       double base_u, base_v;
       if (S.k == 1) {
@@ -132,7 +133,7 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
         base_u = S.Un[q0];
         base_v = S.Vh[(size_t)c * nx + i];
       }
-      const double au = fma(dt, (double)F1, own_u), av = fma(dt, (double)F2, own_v);
+      const double au = fma(dt, to_f64(F1), own_u), av = fma(dt, to_f64(F2), own_v);
       double ou, ov;
       if (S.k == 1) { ou = au; ov = av; }
       else if (S.k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
@@ -148,10 +149,11 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
     for (int c = 0; c < NC; ++c) ua[c] = outv[c * NM];
     bool bad = false;
 #pragma unroll
-    for (int q = 0; q < NC * NM; ++q) bad |= !isfinite(outv[q]);
+    for (int q = 0; q < NC * NM; ++q) bad |= !finite_bits(outv[q]);
     if constexpr (EQ == EQ_EULER) {
-      bad |= !euler_physical<1>(P, ua);
-      if (!bad) wmax = euler_speed<1>(P, 0, ua);
+      double s0, s1;
+      bad |= !euler_speeds<1>(P, ua, s0, s1);
+      if (!bad) wmax = s0;
     } else {
       wmax = Phys<EQ, double>::speed(P, 0, ua);
     }

@@ -284,3 +284,44 @@ def test_engine_shared_by_threads():
     assert not errs, errs
     for q in range(4):
         np.testing.assert_array_equal(outs[q], _solo(ps[q], ws[q].U0, 0.02)[0])
+
+
+def test_failed_request_does_not_disturb_the_others():
+    """A request whose state becomes non-physical (a negative energy planted in one cell) is
+    retired with HWENO_ERR_NONPHYSICAL; the requests served with it finish and give the result
+    they give when served alone."""
+    good = []
+    for seed, n, T in ((30, 64, 0.02), (31, 96, 0.015), (32, 48, 0.03)):
+        w = I.quadrant_vortex_2d(seed, n)
+        good.append((w, _prob2d(w, T), T))
+    wb = I.quadrant_vortex_2d(33, 64)
+    Ub = wb.U0.copy()
+    Ub[3, 0, 30, 30] = -5.0
+    pb = _prob2d(wb, 0.02)
+    eng = H.hweno_create()
+    try:
+        tickets = [H.hweno_submit(eng, p, w.U0) for w, p, T in good]
+        tb = H.hweno_submit(eng, pb, Ub)
+        res, failed = {}, None
+        for _ in range(100000):
+            H.hweno_serve(eng, 8)
+            for tk, (w, p, T) in zip(tickets, good):
+                if tk in res:
+                    continue
+                out = np.empty_like(w.U0)
+                rc, info = H.hweno_poll(eng, tk, out)
+                if rc == H.HWENO_OK:
+                    res[tk] = out
+            if failed is None:
+                try:
+                    rc, info = H.hweno_poll(eng, tb, np.empty_like(Ub))
+                except H.HwenoError as e:
+                    failed = e.code
+            if len(res) == len(tickets) and failed is not None:
+                break
+    finally:
+        H.hweno_destroy(eng)
+    assert failed == H.HWENO_ERR_NONPHYSICAL
+    for tk, (w, p, T) in zip(tickets, good):
+        alone, _ = _served([(w, p, T)])[0]
+        np.testing.assert_array_equal(res[tk], alone)
