@@ -37,18 +37,18 @@ UNIT = "cell-stage/s"
 FP64_PEAK_TFLOPS = 1.19
 FP32_PEAK_TFLOPS = 74.2
 # FP64 flops per cell-stage of the fused 2D Euler characteristic kernel: 2 x DFMA + DMUL + DADD
-# thread instructions of one 2048^2 launch (ncu) per updated cell, 5667, less the 2.5 % of
+# thread instructions of one 2048^2 launch (ncu) per updated cell, 5580, less the 2.5 % of
 # redundant ring-cell reconstruction (profiles/stage2d_euler_2048_instruction_counts.md)
-FP64_FLOPS_PER_CELL_STAGE = 5529.0
+FP64_FLOPS_PER_CELL_STAGE = 5443.0
 # DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
-FP64_STAGE_DRAM_BYTES = 425.7e6 + 669.4e6
+FP64_STAGE_DRAM_BYTES = 423.6e6 + 669.0e6
 # FP64 pipe utilisation of the same kernel (same capture, % of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.856
+FP64_PIPE_UTIL_NCU = 0.855
 # FP32-bulk kernel (same workload, ncu): FP64-pipe thread slots (FP64 arithmetic, f32 <-> f64
 # conversions, compares) and FP32 flops per cell-stage; the FP64 pipe issues one thread slot
 # per lane per clock, i.e. half the FP64 FMA flop rate
 FP32BULK_FP64_SLOTS_PER_CELL_STAGE = 1091.0
-FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4291.0
+FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4184.0
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 

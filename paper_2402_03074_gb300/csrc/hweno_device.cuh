@@ -604,6 +604,8 @@ struct Eig1 {
 template <typename R>
 struct Eig2 {
   R un, ut, c, H, q2h, b1h, b2h, hic;  // un: normal velocity, ut: tangential velocity
+  R bun, but, hun;                     // b1h un, b1h ut, hic un (shared by every projection)
+  R unc, qmH;                          // un c, q2h - H (shared by every unprojection)
   int dir;
   __device__ __forceinline__ bool init(const KProblem& P, int d, const R* U) {
     dir = d;
@@ -621,14 +623,20 @@ struct Eig2 {
     b1h = R(0.5) * gm1 * (rc * rc);
     b2h = q2h * b1h;
     hic = R(0.5) * rc;
+    bun = b1h * un;
+    but = b1h * ut;
+    hun = hic * un;
+    unc = un * c;
+    qmH = q2h - H;
     return p > R(0) && U[0] > R(0);
   }
-  // W = L U for all four fields (the terms s and t are shared by the acoustic fields)
+  // W = L U for all four fields (the terms s and t are shared by the acoustic fields):
+  // s = b2h U0 - b1h (un mn + ut mt - U3), t = hic (un U0 - mn)
   __device__ __forceinline__ void project_all(const R* U, R* W) const {
     const R mn = dir == 0 ? U[1] : U[2];
     const R mt = dir == 0 ? U[2] : U[1];
-    const R s = b2h * U[0] - b1h * (un * mn + ut * mt - U[3]);
-    const R t = (un * U[0] - mn) * hic;
+    const R s = b2h * U[0] + (b1h * U[3] - but * mt - bun * mn);
+    const R t = hun * U[0] - hic * mn;
     W[0] = s + t;
     W[1] = U[0] - R(2) * s;
     W[2] = mt - ut * U[0];
@@ -652,7 +660,8 @@ struct Eig2 {
     const R mt = ut * S + W[2];
     U[0] = S;
     if (dir == 0) { U[1] = mn; U[2] = mt; } else { U[1] = mt; U[2] = mn; }
-    U[3] = H * (W[0] + W[3]) + (un * c) * D + q2h * W[1] + ut * W[2];
+    // H (W0 + W3) + q2h W1 = H S + (q2h - H) W1
+    U[3] = H * S + (qmH * W[1] + (unc * D + ut * W[2]));
   }
   // U += R[:, f] * w for field f
   __device__ __forceinline__ void unproject_add(int f, R w, R* U) const {

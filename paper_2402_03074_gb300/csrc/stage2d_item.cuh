@@ -157,7 +157,8 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           for (int c = 0; c < NC; ++c) {
             const R uR = trL[((c * 3 + g) * 2 + 0) * BW + t + 1];
             const R fR = trL[((c * 3 + g) * 2 + 1) * BW + t + 1];
-            fhx(c * 3 + g, t + 1) = R(0.5) * (fr[g][c] + fR - a1 * (uR - xr[g][c]));
+            // twice the LF flux (Eq. 2.4 without its factor 1/2, folded into the weights)
+            fhx(c * 3 + g, t + 1) = fr[g][c] + fR - a1 * (uR - xr[g][c]);
           }
       }
       __syncthreads();
@@ -167,9 +168,9 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           const R L0 = fhx(c * 3 + 0, t), L1 = fhx(c * 3 + 1, t), L2 = fhx(c * 3 + 2, t);
           const R R0 = fhx(c * 3 + 0, t + 1), R1 = fhx(c * 3 + 1, t + 1),
                   R2 = fhx(c * 3 + 2, t + 1);
-          const R sdiff = R(GW0) * ((R0 - L0) + (R2 - L2)) + R(GW1) * (R1 - L1);
-          const R ssum = R(GW0) * ((L0 + R0) + (L2 + R2)) + R(GW1) * (L1 + R1);
-          const R smom = R(GW0) * s15 * ((R2 - L2) - (R0 - L0));
+          const R sdiff = R(0.5 * GW0) * ((R0 - L0) + (R2 - L2)) + R(0.5 * GW1) * (R1 - L1);
+          const R ssum = R(0.5 * GW0) * ((L0 + R0) + (L2 + R2)) + R(0.5 * GW1) * (L1 + R1);
+          const R smom = R(0.5 * GW0) * s15 * ((R2 - L2) - (R0 - L0));
           rx[c][0] = -sdiff * idx;
           rx[c][1] = (volf[c] - R(0.5) * ssum) * idx;
           rx[c][2] = -smom * idx;
@@ -331,11 +332,11 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
       for (int g = 0; g < 3; ++g)
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          gh[g][c] = R(0.5) * (prevTg[g][c] + ybg[g][c] - a2 * (yb[g][c] - prevT[g][c]));
+          gh[g][c] = prevTg[g][c] + ybg[g][c] - a2 * (yb[g][c] - prevT[g][c]);  // 2 x LF flux
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        const R sw = R(GW0) * (gh[0][c] + gh[2][c]) + R(GW1) * gh[1][c];
-        const R sm = R(GW0) * s15 * (gh[2][c] - gh[0][c]);
+        const R sw = R(0.5 * GW0) * (gh[0][c] + gh[2][c]) + R(0.5 * GW1) * gh[1][c];
+        const R sm = R(0.5 * GW0) * s15 * (gh[2][c] - gh[0][c]);
         // top face of (i, j-1): F1 -= sum/dy, F2 -= sum xi/dy, F3 -= sum/(2 dy)
         pend[c][0] -= sw * idy;
         pend[c][1] -= sm * idy;
