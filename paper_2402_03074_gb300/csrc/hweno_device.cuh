@@ -531,16 +531,6 @@ __device__ __forceinline__ double euler_speed(const KProblem& P, int dir, const 
   return fabs(dir == 0 ? vx : vy) + sqrt(P.gam * p * ir);
 }
 
-template <int DIM>
-__device__ __forceinline__ bool euler_physical(const KProblem& P, const double* u) {
-  if (!(u[0] > 0.0)) return false;
-  double kin;
-  if (DIM == 1) kin = 0.5 * u[1] * u[1] / u[0];
-  else kin = 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0];
-  const double e = u[DIM + 1] - kin;
-  return e > 0.0 && isfinite(e);
-}
-
 // Admissibility of an output average (rho > 0, internal energy > 0 and finite) and its wave
 // speeds |u| + c, |v| + c in one pass: one reciprocal of rho and one square root.
 template <int DIM>
@@ -584,12 +574,6 @@ struct Eig1 {
     W[0] = s + t;
     W[1] = U[0] - R(2) * s;
     W[2] = s - t;
-  }
-  __device__ __forceinline__ R project_field(int f, const R* U) const {
-    const R s = b2h * U[0] - b1h * (u * U[1] - U[2]);
-    if (f == 1) return U[0] - R(2) * s;
-    const R t = (u * U[0] - U[1]) * hic;
-    return f == 0 ? s + t : s - t;
   }
   // U = R W
   __device__ __forceinline__ void unproject(const R* W, R* U) const {
@@ -642,16 +626,6 @@ struct Eig2 {
     W[2] = mt - ut * U[0];
     W[3] = s - t;
   }
-  // components in the rotated frame: n = normal momentum, t = tangential momentum
-  __device__ __forceinline__ R project_field(int f, const R* U) const {
-    const R mn = dir == 0 ? U[1] : U[2];
-    const R mt = dir == 0 ? U[2] : U[1];
-    if (f == 2) return mt - ut * U[0];              // shear
-    const R s = b2h * U[0] - b1h * (un * mn + ut * mt - U[3]);
-    if (f == 1) return U[0] - R(2) * s;             // entropy
-    const R t = (un * U[0] - mn) * hic;
-    return f == 0 ? s + t : s - t;                  // u-c, u+c
-  }
   // U = R W (columns u-c, u, shear, u+c in the rotated frame)
   __device__ __forceinline__ void unproject(const R* W, R* U) const {
     const R S = W[0] + W[1] + W[3];
@@ -662,17 +636,6 @@ struct Eig2 {
     if (dir == 0) { U[1] = mn; U[2] = mt; } else { U[1] = mt; U[2] = mn; }
     // H (W0 + W3) + q2h W1 = H S + (q2h - H) W1
     U[3] = H * S + (qmH * W[1] + (unc * D + ut * W[2]));
-  }
-  // U += R[:, f] * w for field f
-  __device__ __forceinline__ void unproject_add(int f, R w, R* U) const {
-    R mn, mt, e, r0;
-    if (f == 0) { r0 = w; mn = (un - c) * w; mt = ut * w; e = (H - un * c) * w; }
-    else if (f == 1) { r0 = w; mn = un * w; mt = ut * w; e = q2h * w; }
-    else if (f == 2) { r0 = R(0); mn = R(0); mt = w; e = ut * w; }
-    else { r0 = w; mn = (un + c) * w; mt = ut * w; e = (H + un * c) * w; }
-    U[0] += r0;
-    if (dir == 0) { U[1] += mn; U[2] += mt; } else { U[1] += mt; U[2] += mn; }
-    U[3] += e;
   }
 };
 
