@@ -33,21 +33,25 @@ N_DEFAULT = 2048
 METRIC = "cell-stage updates/s (2D Euler 2048^2, FP32 vs FP64 at stated L1 err); p50/p99 solve"
 UNIT = "cell-stage/s"
 # measured peaks (MEASURED_PEAKS.json holds HBM / bf16; FP64 and FP32 FMA rates were
-# measured on this machine's GB300 with an FMA-chain probe: 1.19 TFLOP/s FP64, 74 TFLOP/s FP32)
+# measured on this machine's GB300 with an FMA-chain probe: 1.19 TFLOP/s FP64, 74 TFLOP/s FP32).
+# The FP64 pipe executes one operation (FMA, multiply or add) per lane per clock, so its
+# operation rate is half the FMA flop rate: 0.595 TOP/s.
 FP64_PEAK_TFLOPS = 1.19
+FP64_PEAK_TOPS = FP64_PEAK_TFLOPS / 2.0
 FP32_PEAK_TFLOPS = 74.2
-# FP64 flops per cell-stage of the fused 2D Euler characteristic kernel: 2 x DFMA + DMUL + DADD
-# thread instructions of one 2048^2 launch (ncu) per updated cell, 5580, less the 2.5 % of
-# redundant ring-cell reconstruction (profiles/stage2d_euler_2048_instruction_counts.md)
+# FP64 arithmetic of the fused 2D Euler characteristic kernel per cell-stage, from the ncu
+# thread-instruction counts of one 2048^2 launch (profiles/stage2d_euler_2048_instruction_
+# counts.md) per updated cell less the 2.5 % of redundant ring-cell reconstruction:
+# operations (DFMA + DMUL + DADD) 3675 -> 3585, flops (2 DFMA + DMUL + DADD) 5580 -> 5443
+FP64_OPS_PER_CELL_STAGE = 3585.0
 FP64_FLOPS_PER_CELL_STAGE = 5443.0
 # DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
 FP64_STAGE_DRAM_BYTES = 423.6e6 + 669.0e6
 # FP64 pipe utilisation of the same kernel (same capture, % of peak sustained, active cycles)
 FP64_PIPE_UTIL_NCU = 0.855
-# FP32-bulk kernel (same workload, ncu): FP64-pipe thread slots (FP64 arithmetic, f32 <-> f64
-# conversions, compares) and FP32 flops per cell-stage; the FP64 pipe issues one thread slot
-# per lane per clock, i.e. half the FP64 FMA flop rate
-FP32BULK_FP64_SLOTS_PER_CELL_STAGE = 1091.0
+# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (1017 per
+# updated cell less 2.9 % ring redundancy at three blocks per SM) and FP32 flops
+FP32BULK_FP64_OPS_PER_CELL_STAGE = 988.0
 FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4184.0
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
@@ -283,14 +287,13 @@ def run_ours(args):
         diff = np.abs(out32[:, 0] - out64[:, 0])
         scale = np.abs(out64[:, 0]).mean(axis=(1, 2))[:, None, None]
         k32_ms = stage_kernel_ms(prob(H.HWENO_MIXED32))
-        slots = FP32BULK_FP64_SLOTS_PER_CELL_STAGE * n * n / (k32_ms / 1e3)
+        ops32 = FP32BULK_FP64_OPS_PER_CELL_STAGE * n * n / (k32_ms / 1e3) / 1e12
         mixed = {"value": world * cell_stages / (ms32 / 1e3), "unit": UNIT, "dtype": "f32+f64",
                  "ms_per_step": ms32 / args.steps,
-                 "roofline": {"bound": "fp64 pipe", "kernel_ms": k32_ms,
-                              "fp64_pipe_slots_per_cell_stage": FP32BULK_FP64_SLOTS_PER_CELL_STAGE,
-                              "achieved_slots_per_s": slots,
-                              "peak_slots_per_s": FP64_PEAK_TFLOPS * 1e12 / 2.0,
-                              "frac": slots / (FP64_PEAK_TFLOPS * 1e12 / 2.0),
+                 "roofline": {"bound": "alu (FP64 share)", "unit": "TOP/s (FP64 operations)",
+                              "kernel_ms": k32_ms, "achieved": ops32, "peak": FP64_PEAK_TOPS,
+                              "frac": ops32 / FP64_PEAK_TOPS,
+                              "fp64_ops_per_cell_stage": FP32BULK_FP64_OPS_PER_CELL_STAGE,
                               "fp32_tflops": FP32BULK_FP32_FLOPS_PER_CELL_STAGE * n * n /
                                              (k32_ms / 1e3) / 1e12,
                               "fp32_peak_tflops": FP32_PEAK_TFLOPS},
@@ -340,16 +343,23 @@ def run_ours(args):
 
     if rank != 0:
         return
-    flops = FP64_FLOPS_PER_CELL_STAGE
-    achieved = flops * n * n / (k_ms / 1e3) / 1e12 if flops else None
-    roofline = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+    # ALU roofline of the FP64 stage kernel: FP64 arithmetic operations per second against
+    # the FP64 pipe's operation rate (the flop view, FMA = 2, is capped at 0.76 by this
+    # kernel's mix of FMA, multiply and add and is reported beside it)
+    ops = FP64_OPS_PER_CELL_STAGE * n * n / (k_ms / 1e3) / 1e12
+    tflops = FP64_FLOPS_PER_CELL_STAGE * n * n / (k_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "unit": "TOP/s (FP64 operations)", "achieved": ops,
+                "peak": FP64_PEAK_TOPS, "frac": ops / FP64_PEAK_TOPS,
                 "traffic": FP64_STAGE_DRAM_BYTES if n == 2048 else None,
                 "fp64_pipe_util_ncu": FP64_PIPE_UTIL_NCU,
                 "kernel": "stage2d_kernel<EULER, characteristic, double>",
-                "kernel_ms": k_ms, "flops_per_cell_stage": flops,
+                "kernel_ms": k_ms, "ops_per_cell_stage": FP64_OPS_PER_CELL_STAGE,
+                "flop_view": {"achieved_tflops": tflops, "peak_tflops": FP64_PEAK_TFLOPS,
+                              "frac": tflops / FP64_PEAK_TFLOPS,
+                              "flops_per_cell_stage": FP64_FLOPS_PER_CELL_STAGE},
                 "hbm_GBps": ALGO_BYTES_PER_CELL_STAGE * n * n / (k_ms / 1e3) / 1e9,
-                "peak_note": "FP64 FMA rate measured on this pool's GB300 (of measured)"}
+                "peak_note": "FP64 pipe rate from the FMA rate measured on this pool's GB300 "
+                             "(of measured): one operation per lane per clock"}
     # launches in the timed region: hweno_advance replays a captured graph of four steps (dt +
     # three stage kernels each), ceil(K / 4) times for K steps; the steps past the limit in the
     # last replay launch and return at once
