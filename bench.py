@@ -45,10 +45,12 @@ FP32_PEAK_TFLOPS = 74.2
 # operations (DFMA + DMUL + DADD) 3675 -> 3585, flops (2 DFMA + DMUL + DADD) 5580 -> 5443
 FP64_OPS_PER_CELL_STAGE = 3585.0
 FP64_FLOPS_PER_CELL_STAGE = 5443.0
-# DRAM bytes read + written by one FP64 stage launch at 2048^2 (same ncu capture)
-FP64_STAGE_DRAM_BYTES = 423.6e6 + 669.0e6
-# FP64 pipe utilisation of the same kernel (same capture, % of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.855
+# DRAM bytes read + written by one FP64 stage launch at 2048^2 in its default launch
+# geometry (22 bands of 94 columns, 13 row chunks; ncu, profiles/stage2d_euler_2048_
+# instruction_counts.md)
+FP64_STAGE_DRAM_BYTES = 421.9e6 + 643.0e6
+# FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
+FP64_PIPE_UTIL_NCU = 0.836
 # FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (1017 per
 # updated cell less 2.9 % ring redundancy at three blocks per SM) and FP32 flops
 FP32BULK_FP64_OPS_PER_CELL_STAGE = 988.0
@@ -241,6 +243,19 @@ def run_ours(args):
         H.hweno_close(eng, sid)
         return ms, out
 
+    # launch-geometry autotuner (before any timing, like compilation): the tile shape of the
+    # 2D stage kernel for this grid in both precisions, kept in the process's tuning table
+    # and used by every later launch of such a problem
+    tiles = {}
+    if args.tuning_file:
+        tiles = {"loaded": args.tuning_file, "entries": H.hweno_tuning_load(args.tuning_file)}
+    elif not args.no_autotune:
+        for name, prec in (("fp64", H.HWENO_FP64), ("mixed32", H.HWENO_MIXED32)):
+            r, b, ms = H.hweno_autotune(eng, prob(prec), U0)
+            tiles[name] = {"rows": r, "bands": b, "stage_ms": ms}
+        if args.save_tuning:
+            H.hweno_tuning_save(args.save_tuning)
+
     # headline: FP64 path
     with ClockSampler(dev) as clk:
         ms64, out64 = timed_steps(H.HWENO_FP64, args.steps, args.warmup)
@@ -304,7 +319,8 @@ def run_ours(args):
 
     longr = None
     if args.long_steps > 0:
-        longr = long_runs(H, I, eng, stream, U0, w.bc, n, args.long_steps)
+        longr = long_runs(H, I, eng, stream, U0, w.bc, n, args.long_steps,
+                          autotune=not args.no_autotune)
 
     # end to end through the C ABI with host buffers: per step H2D of the state from pinned
     # memory, one step, D2H of the new state
@@ -366,7 +382,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": _workload_config(n), "gpu_launches": 16 * math.ceil(args.steps / 4),
+            "config": _workload_config(n, {"tile_shape": tiles or "default"}),
+            "gpu_launches": 16 * math.ceil(args.steps / 4),
             "clocks": clk.summary(), "roofline": roofline, "mixed32": mixed, "e2e": e2e,
             "served": served, "tubes_1d": tubes, "long_runs": longr}
     if world == 1 and not args.no_cpu_baseline:
@@ -448,7 +465,7 @@ def served_stream(H, I, eng_factory, m, rate, grids, t_lo, t_hi, seed=0):
             "speedup_solves_per_s": served["solves_per_s"] / plain["solves_per_s"]}
 
 
-def long_runs(H, I, eng, stream, U0, bc, n, steps):
+def long_runs(H, I, eng, stream, U0, bc, n, steps, autotune=True):
     """The long 2D Euler runs: `steps` FP64 steps of the 1024^2 quadrant + vortex state (seed
     1) with its conservation drift (transmissive: the net boundary flux), and `steps` steps of
     the n^2 state in FP64 and in the FP32-bulk path from identical inputs, with the L1 / Linf
@@ -473,6 +490,8 @@ def long_runs(H, I, eng, stream, U0, bc, n, steps):
 
     w3 = I.quadrant_vortex_2d(1, 1024)
     p3 = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=1024, ny=1024, bc=w3.bc, cfl=0.6)
+    if autotune:
+        H.hweno_autotune(eng, p3, w3.U0)
     _, t3, ms3, drift3 = run(p3, w3.U0)
     res = {"c3": {"workload": f"2D Euler quadrant+vortex 1024x1024 (seed 1), FP64, {steps} steps",
                   "cell_stages_per_s": 1024 * 1024 * 3 * steps / (ms3 / 1e3), "t": t3,
@@ -641,6 +660,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-tubes", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the default launch geometry instead of the autotuned one")
+    ap.add_argument("--save-tuning", default="", help="write the autotuned table to this file")
+    ap.add_argument("--tuning-file", default="",
+                    help="load the tuning table from this file instead of autotuning")
     ap.add_argument("--long-steps", type=int, default=200,
                     help="steps of the long 1024^2 / 2048^2 runs (0: skip them)")
     ap.add_argument("--tubes", type=int, default=16)

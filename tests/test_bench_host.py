@@ -99,6 +99,7 @@ def test_replica_throughput_and_config():
 def test_long_runs_report():
     H = _fake_binding()
     H.hweno_conservation = lambda eng, sid, nc: (np.ones(nc), np.ones(nc) * 2.0)
+    H.hweno_autotune = lambda eng, p, U: (0, 0, 1.0)
 
     class _Ev:
         def __init__(self, **kw):

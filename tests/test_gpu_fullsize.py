@@ -36,16 +36,19 @@ def _edges(n, width, pad=2):
 
 def _sample_cells(n, seed):
     """Flat indices j * n + i: the crossings of the band edges (columns) and row-chunk edges
-    (rows) of the 2D launch geometry (128-thread bands of at most 126 output columns; row
-    chunks of two resident blocks per SM on 152 SMs), the domain edges, and random cells."""
-    bands = (n + 125) // 126
-    wout = (n + bands - 1) // bands
-    ch = max(1, min(n, 304 // bands))
-    rows = (n + ch - 1) // ch
-    cols = _edges(n, wout)
-    rws = _edges(n, rows)
+    (rows) of the 2D launch layouts (128-thread blocks, 304 resident slots for FP64, 456 for
+    FP32-bulk; bands of at most 126 or, for FP64, at most 94 columns), the domain edges, and
+    random cells."""
+    cols, rws = set(), set()
+    for wmax in (126, 94):
+        bands = (n + wmax - 1) // wmax
+        wout = (n + bands - 1) // bands
+        cols |= set(_edges(n, wout))
+        for slots in (304, 456):
+            ch = max(1, min(n, slots // bands))
+            rws |= set(_edges(n, (n + ch - 1) // ch))
     rng = np.random.default_rng(seed)
-    edge = [j * n + i for j in rws for i in cols]
+    edge = [j * n + i for j in sorted(rws) for i in sorted(cols)]
     rnd = rng.integers(0, n * n, size=2000).tolist()
     side = [j * n + i for j in rng.integers(0, n, size=300) for i in (0, 1, n - 2, n - 1)]
     side += [j * n + i for i in rng.integers(0, n, size=300) for j in (0, 1, n - 2, n - 1)]
