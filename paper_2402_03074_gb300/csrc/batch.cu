@@ -258,10 +258,18 @@ int batch_slots(int cls) {
 
 void batch_geometry1d(int nx, int* blocks) { *blocks = (nx + (kBatchBW - 2) - 1) / (kBatchBW - 2); }
 
-void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks) {
+void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks,
+                    bool lane_aware) {
   constexpr int BW = kBatchBW;
-  *bands = (nx + (BW - 2) - 1) / (BW - 2);
+  int b = (nx + (BW - 2) - 1) / (BW - 2);
+  if (lane_aware) {  // bands of <= BW-34 columns when they leave fewer idle lanes (FP64)
+    auto lanes = [nx](int nb) { return nb * 32 * (((nx + nb - 1) / nb + 2 + 31) / 32); };
+    const int b3 = (nx + (BW - 34) - 1) / (BW - 34);
+    if (b3 <= nx && 100LL * lanes(b3) < 99LL * lanes(b)) b = b3;
+  }
+  *bands = b;
   *wout = (nx + *bands - 1) / *bands;
+  *bands = (nx + *wout - 1) / *wout;
   if (rows < 1) rows = 1;
   *chunks = (ny + rows - 1) / rows;
 }

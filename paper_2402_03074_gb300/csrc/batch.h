@@ -39,7 +39,10 @@ struct BatchDt {
 };
 
 int batch_class(int equation, int characteristic, int mixed, int dim = 2);
-void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks);
+// bands (of at most kBatchBW - 2 columns; lane_aware: of at most kBatchBW - 34 columns when
+// that leaves fewer idle lanes, for the FP64 classes) and row chunks of `rows` rows
+void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks,
+                    bool lane_aware = false);
 void batch_geometry1d(int nx, int* blocks);
 int batch_slots(int cls);  // resident blocks of the class's persistent launch
 cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st);

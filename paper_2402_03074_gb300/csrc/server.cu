@@ -147,7 +147,7 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     if (!batched(p) || p->dim != 2) continue;
     const int cls = class_of(p);
     int bands, wout, chunks;
-    batch_geometry(p->nx, p->ny, 1, &bands, &wout, &chunks);
+    batch_geometry(p->nx, p->ny, 1, &bands, &wout, &chunks, p->precision != HWENO_MIXED32);
     band_rows[cls] += (long long)bands * p->ny;
   }
   int rows_of[kBatchClasses];
@@ -177,7 +177,7 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     B.mixed = p->precision == HWENO_MIXED32;
     if (p->dim == 2) {
       B.rows = rows_of[cls];
-      batch_geometry(p->nx, p->ny, B.rows, &B.bands, &B.wout, &B.chunks);
+      batch_geometry(p->nx, p->ny, B.rows, &B.bands, &B.wout, &B.chunks, !B.mixed);
     } else {
       batch_geometry1d(p->nx, &B.bands);
       B.wout = kBatchBW - 2;
