@@ -8,7 +8,7 @@
 //   2. advances every live solve by a few time steps: one replay of a captured step graph =
 //      one batched dt launch (each solve its own dt) + per kernel class three persistent
 //      stage launches over the work items of all live solves of that class (1D and 2D
-//      solves are separate classes);
+//      solves are separate classes; the classes are parallel branches of the graph);
 //   3. reads the scalars of all live solves back in one copy and retires the finished ones
 //      (result copied to host memory, device memory released, work lists rewritten).
 // Requests that arrive while others run are admitted at the next iteration: their work
@@ -63,6 +63,10 @@ struct Server {
   DevScal* h_gather = nullptr;  // pinned
   cudaGraphExec_t graph = nullptr;
   unsigned graph_classes = 0;   // bit mask of the classes the graph launches
+  // side streams and events of the step graph's per-class branches
+  cudaStream_t side[kBatchClasses] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kBatchClasses] = {};
   bool dirty = true;
   int rows = 32;                // rows per work item
   // background thread
@@ -94,6 +98,11 @@ static int server_alloc(Server* S) {
   if (c == cudaSuccess) c = cudaMallocHost(&S->h_ctl, sizeof(BatchCtl) * kBatchClasses);
   if (c == cudaSuccess) c = cudaMalloc(&S->d_gather, sizeof(DevScal) * kBatchCap);
   if (c == cudaSuccess) c = cudaMallocHost(&S->h_gather, sizeof(DevScal) * kBatchCap);
+  if (c == cudaSuccess) c = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming);
+  for (int q = 1; q < kBatchClasses && c == cudaSuccess; ++q) {
+    c = cudaStreamCreateWithFlags(&S->side[q], cudaStreamNonBlocking);
+    if (c == cudaSuccess) c = cudaEventCreateWithFlags(&S->ev_join[q], cudaEventDisableTiming);
+  }
   if (c != cudaSuccess) {
     cudaGetLastError();
     return HWENO_ERR_OOM;
@@ -113,6 +122,11 @@ static void server_free(Server* S) {
   cudaFreeHost(S->h_ctl);
   cudaFree(S->d_gather);
   cudaFreeHost(S->h_gather);
+  if (S->ev_fork) cudaEventDestroy(S->ev_fork);
+  for (int q = 1; q < kBatchClasses; ++q) {
+    if (S->side[q]) cudaStreamDestroy(S->side[q]);
+    if (S->ev_join[q]) cudaEventDestroy(S->ev_join[q]);
+  }
 }
 
 static bool batched(const hweno_problem* p) { return p->dim == 1 || p->dim == 2; }
@@ -138,24 +152,24 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
                         [](Request* r) { return batched(&r->prob); });
   int nb[kBatchClasses] = {};
   int items[kBatchClasses] = {};
-  // rows per work item, per class: the items of the class fill its persistent launch's
-  // resident block slots about once (taller items waste fewer ring rows, but a launch with
-  // fewer items than slots leaves SMs idle, e.g. when few solves are left)
-  long long band_rows[kBatchClasses] = {};
+  // rows per work item, per class: the fewest waves of items over the class's resident
+  // block slots for the length of its launch (a partial last wave costs a whole item time;
+  // taller items waste fewer ring rows, but fewer items than slots leave SMs idle)
+  std::vector<int> cb[kBatchClasses], cy[kBatchClasses];
   for (Request* r : S->live) {
     const hweno_problem* p = solve_problem(r->solve);
     if (!batched(p) || p->dim != 2) continue;
     const int cls = class_of(p);
     int bands, wout, chunks;
     batch_geometry(p->nx, p->ny, 1, &bands, &wout, &chunks, p->precision != HWENO_MIXED32);
-    band_rows[cls] += (long long)bands * p->ny;
+    cb[cls].push_back(bands);
+    cy[cls].push_back(p->ny);
   }
   int rows_of[kBatchClasses];
-  for (int c = 0; c < kBatchClasses; ++c) {
-    const int slots = batch_slots(c);
-    long long r = slots > 0 ? band_rows[c] / slots : S->rows;
-    rows_of[c] = (int)(r < 4 ? 4 : (r > 64 ? 64 : r));
-  }
+  for (int c = 0; c < kBatchClasses; ++c)
+    rows_of[c] = cb[c].empty() ? S->rows
+                               : batch_rows(cb[c].data(), cy[c].data(), (int)cb[c].size(),
+                                            batch_slots(c));
   int n = 0, nall = 0;
   *classes = 0;
   for (Request* r : S->live) {
@@ -207,12 +221,27 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
   return HWENO_OK;
 }
 
-// one step of every live batched solve
+// one step of every live batched solve: the dt launch, then per class its three stage
+// launches.  Every solve belongs to one class, so the classes' stage chains share no data and
+// run as parallel branches (forked from and joined back into st): the blocks of one class's
+// launch take the SMs that another class's launch leaves idle in its last wave.
 static cudaError_t enqueue_batch_step(Server* S, unsigned classes, cudaStream_t st) {
   cudaError_t e = launch_batch_dt(S->d_dt, S->d_ctl, kBatchClasses, kBatchCap, st);
-  for (int k = 1; k <= 3 && e == cudaSuccess; ++k)
-    for (int c = 0; c < kBatchClasses && e == cudaSuccess; ++c)
-      if (classes & (1u << c)) e = launch_batch_stage(c, S->d_bs + c * kBatchCap, S->d_ctl + c, k, st);
+  int list[kBatchClasses], nc = 0;
+  for (int c = 0; c < kBatchClasses; ++c)
+    if (classes & (1u << c)) list[nc++] = c;
+  if (e == cudaSuccess && nc > 1) e = cudaEventRecord(S->ev_fork, st);
+  for (int q = 1; q < nc && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(S->side[q], S->ev_fork, 0);
+  for (int q = 0; q < nc && e == cudaSuccess; ++q) {
+    const int c = list[q];
+    cudaStream_t sq = q == 0 ? st : S->side[q];
+    for (int k = 1; k <= 3 && e == cudaSuccess; ++k)
+      e = launch_batch_stage(c, S->d_bs + c * kBatchCap, S->d_ctl + c, k, sq);
+  }
+  for (int q = 1; q < nc && e == cudaSuccess; ++q) {
+    e = cudaEventRecord(S->ev_join[q], S->side[q]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, S->ev_join[q], 0);
+  }
   return e;
 }
 

@@ -191,18 +191,17 @@ extern "C" int hweno_stage_batch_static(int n, const hweno_problem* problems, in
   size_t limit = 0;
   if (cudaDeviceGetLimit(&limit, cudaLimitStackSize) != cudaSuccess) return HWENO_ERR_CUDA;
   if (D.local[cls] > limit) return HWENO_ERR_STATE;
-  // work list: one item per (band, row chunk); row chunks sized so the items fill the
-  // resident block slots about once
+  // work list: one item per (band, row chunk); the rows per chunk give the launch the fewest
+  // waves of items over the resident block slots for its length
   StaticScratch host;
   std::memset(&host, 0, sizeof(host));
-  long long band_rows = 0;
   int bands[HWENO_STATIC_BATCH_MAX], wout[HWENO_STATIC_BATCH_MAX], chunks[HWENO_STATIC_BATCH_MAX];
+  int nys[HWENO_STATIC_BATCH_MAX];
   for (int s = 0; s < n; ++s) {
     batch_geometry(problems[s].nx, problems[s].ny, 1, &bands[s], &wout[s], &chunks[s]);
-    band_rows += (long long)bands[s] * problems[s].ny;
+    nys[s] = problems[s].ny;
   }
-  long long rows = band_rows / (D.slots[cls] > 0 ? D.slots[cls] : 1);
-  rows = rows < 4 ? 4 : (rows > 64 ? 64 : rows);
+  const int rows = batch_rows(bands, nys, n, D.slots[cls]);
   int items = 0;
   for (int s = 0; s < n; ++s) {
     StaticItem& it = host.item[s];
@@ -217,7 +216,7 @@ extern "C" int hweno_stage_batch_static(int n, const hweno_problem* problems, in
     it.status = status[s];
     it.bands = bands[s];
     it.wout = wout[s];
-    it.rows = (int)rows;
+    it.rows = rows;
     it.chunks = (problems[s].ny + it.rows - 1) / it.rows;
     it.item_base = items;
     items += it.bands * it.chunks;
