@@ -15,8 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhweno.so")
 SOURCES = ["stage1d.cu", "stage2d.cu", "batch.cu", "engine.cu", "server.cu", "tune.cu",
            "static_batch.cu"]
-HEADERS = ["hweno_device.cuh", "launch.h", "server.h", "batch.h", "stage1d_item.cuh",
-           "stage2d_item.cuh"]
+HEADERS = ["hweno_device.cuh", "launch.h", "server.h", "batch.h", "geometry.h",
+           "stage1d_item.cuh", "stage2d_item.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "-I" + os.path.join(ROOT, "include")]

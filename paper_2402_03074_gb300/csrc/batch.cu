@@ -258,43 +258,9 @@ int batch_slots(int cls) {
 
 void batch_geometry1d(int nx, int* blocks) { *blocks = (nx + (kBatchBW - 2) - 1) / (kBatchBW - 2); }
 
-// A persistent launch over `items` work items runs ceil(items / slots) waves, and a block's
-// time per item grows with the item's rows plus about 1.5 rows of fixed cost (the two ring
-// rows of the y pass and the four-row window prologue); a block alone on an SM is not faster
-// than one of two sharing it (each block's row sweep is bound by its own instruction
-// latency).  So the rows minimising waves x (rows + 1.5) give the shortest launch; among
-// equal costs the smallest rows (the most items, the best balance) win.
-int batch_rows(const int* bands, const int* ny, int n, int slots) {
-  if (n <= 0 || slots <= 0) return 32;
-  int nymax = 1;
-  for (int s = 0; s < n; ++s) nymax = ny[s] > nymax ? ny[s] : nymax;
-  int best = 4;
-  double best_cost = 1e300;
-  for (int r = 4; r <= (nymax > 4 ? nymax : 4); ++r) {
-    long long items = 0;
-    for (int s = 0; s < n; ++s) items += (long long)bands[s] * ((ny[s] + r - 1) / r);
-    const long long waves = (items + slots - 1) / slots;
-    const double cost = (double)waves * (r + 1.5);
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = r;
-    }
-  }
-  return best;
-}
-
 void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks,
                     bool lane_aware) {
-  constexpr int BW = kBatchBW;
-  int b = (nx + (BW - 2) - 1) / (BW - 2);
-  if (lane_aware) {  // bands of <= BW-34 columns when they leave fewer idle lanes (FP64)
-    auto lanes = [nx](int nb) { return nb * 32 * (((nx + nb - 1) / nb + 2 + 31) / 32); };
-    const int b3 = (nx + (BW - 34) - 1) / (BW - 34);
-    if (b3 <= nx && 100LL * lanes(b3) < 99LL * lanes(b)) b = b3;
-  }
-  *bands = b;
-  *wout = (nx + *bands - 1) / *bands;
-  *bands = (nx + *wout - 1) / *wout;
+  split_bands(nx, default_bands(nx, kBatchBW, lane_aware), bands, wout);
   if (rows < 1) rows = 1;
   *chunks = (ny + rows - 1) / rows;
 }

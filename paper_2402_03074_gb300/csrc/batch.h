@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "geometry.h"
 #include "launch.h"
 
 namespace hw {
@@ -44,9 +45,6 @@ int batch_class(int equation, int characteristic, int mixed, int dim = 2);
 void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks,
                     bool lane_aware = false);
 void batch_geometry1d(int nx, int* blocks);
-// rows per work item for the 2D solves of one class (bands[s] bands and ny[s] rows each) whose
-// persistent launch has `slots` resident blocks: the shortest launch by the wave count
-int batch_rows(const int* bands, const int* ny, int n, int slots);
 int batch_slots(int cls);  // resident blocks of the class's persistent launch
 cudaError_t launch_batch_dt(BatchDt* d, BatchCtl* ctl, int nctl, int cap, cudaStream_t st);
 cudaError_t launch_batch_stage(int cls, const BatchSolve* bs, BatchCtl* ctl, int k,

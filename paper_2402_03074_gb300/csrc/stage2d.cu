@@ -1,5 +1,6 @@
 // stage2d.cu -- single-solve launch of the fused 2D HWENO-U stage (one block per band x
 // row chunk; the work item itself is in stage2d_item.cuh).
+#include "geometry.h"
 #include "launch.h"
 #include "stage2d_item.cuh"
 
@@ -13,45 +14,6 @@ __global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];
   stage2d_item<EQ, CHAR, R, BW>(P, S, blockIdx.x, blockIdx.y, rows, wout, smem, red);
-}
-
-// Launch geometry: bands of equal width and row chunks sized so that bands x chunks fills
-// the resident block slots of the GPU once, unless the tuning table (or the autotuner)
-// fixes the tile shape: rows per chunk and/or the band count.  A band of w output columns
-// occupies ceil((w + 2) / 32) warps; with lane_aware set (the FP64 kernels, whose two
-// blocks per SM keep the FP64 pipe busy with three active warps each) the default is the
-// narrower of the bands of at most BW-2 and at most BW-34 columns that leaves fewer idle
-// lanes (2048 columns: 22 bands of 94 columns in 96 lanes each rather than 17 of 121 in 128).
-struct Geom2D {
-  int bands, wout, chunks, rows;
-};
-static int band_lanes(int nx, int bands) {
-  const int w = (nx + bands - 1) / bands;
-  return bands * 32 * ((w + 2 + 31) / 32);
-}
-static Geom2D geom2d(int nx, int ny, int bw, int slots, int rows_fixed, int bands_fixed,
-                     bool lane_aware) {
-  Geom2D g;
-  int bmin = (nx + (bw - 2) - 1) / (bw - 2);
-  if (lane_aware && bw > 34) {
-    const int b3 = (nx + (bw - 34) - 1) / (bw - 34);
-    if (b3 <= nx && 100LL * band_lanes(nx, b3) < 99LL * band_lanes(nx, bmin)) bmin = b3;
-  }
-  g.bands = bands_fixed > 0 ? (bands_fixed < nx ? bands_fixed : nx) : bmin;
-  if (bands_fixed > 0 && g.bands < (nx + (bw - 2) - 1) / (bw - 2))
-    g.bands = (nx + (bw - 2) - 1) / (bw - 2);  // a band is at most BW-2 columns wide
-  g.wout = (nx + g.bands - 1) / g.bands;
-  g.bands = (nx + g.wout - 1) / g.wout;  // no empty band
-  if (rows_fixed > 0) {
-    g.rows = rows_fixed < ny ? rows_fixed : ny;
-  } else {
-    int ch = slots / g.bands;
-    if (ch < 1) ch = 1;
-    if (ch > ny) ch = ny;
-    g.rows = (ny + ch - 1) / ch;
-  }
-  g.chunks = (ny + g.rows - 1) / g.rows;
-  return g;
 }
 
 static thread_local TileShape g_force_shape;
@@ -93,6 +55,8 @@ static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t s
   TileShape t = g_force_shape;  // > 0 fixed, -1 default geometry, {0, 0} consult the table
   if (t.rows == 0 && t.bands == 0)
     t = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, P.ny);
+  // bands of equal width and row chunks filling the resident block slots once, unless the
+  // tuning table (or the autotuner) fixes the tile shape (geometry.h)
   const Geom2D g = geom2d(P.nx, P.ny, BW, slots, t.rows > 0 ? t.rows : 0,
                           t.bands > 0 ? t.bands : 0, sizeof(R) == sizeof(double));
   dim3 grid(g.bands, g.chunks);
