@@ -40,20 +40,19 @@ FP64_PEAK_TFLOPS = 1.19
 FP64_PEAK_TOPS = FP64_PEAK_TFLOPS / 2.0
 FP32_PEAK_TFLOPS = 74.2
 # FP64 arithmetic of the fused 2D Euler characteristic kernel per cell-stage, from the ncu
-# thread-instruction counts of one 2048^2 launch (profiles/stage2d_euler_2048_instruction_
-# counts.md) per updated cell less the 2.5 % of redundant ring-cell reconstruction:
-# operations (DFMA + DMUL + DADD) 3675 -> 3585, flops (2 DFMA + DMUL + DADD) 5580 -> 5443
-FP64_OPS_PER_CELL_STAGE = 3585.0
-FP64_FLOPS_PER_CELL_STAGE = 5443.0
-# DRAM bytes read + written by one FP64 stage launch at 2048^2 in its default launch
-# geometry (22 bands of 94 columns, 13 row chunks; ncu, profiles/stage2d_euler_2048_
-# instruction_counts.md)
-FP64_STAGE_DRAM_BYTES = 421.9e6 + 643.0e6
+# thread-instruction counts of one 2048^2 launch in its default geometry (22 bands of 94
+# columns, 13 row chunks; profiles/stage2d_euler_2048_instruction_counts.md) per updated
+# cell less the 2.8 % of redundant ring-cell reconstruction: operations (DFMA + DMUL + DADD)
+# 3627 -> 3528, flops (2 DFMA + DMUL + DADD) 5478 -> 5329
+FP64_OPS_PER_CELL_STAGE = 3528.0
+FP64_FLOPS_PER_CELL_STAGE = 5329.0
+# DRAM bytes read + written by the same launch (ncu)
+FP64_STAGE_DRAM_BYTES = 423.7e6 + 641.7e6
 # FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.836
-# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (1017 per
+FP64_PIPE_UTIL_NCU = 0.835
+# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (992 per
 # updated cell less 2.9 % ring redundancy at three blocks per SM) and FP32 flops
-FP32BULK_FP64_OPS_PER_CELL_STAGE = 988.0
+FP32BULK_FP64_OPS_PER_CELL_STAGE = 963.0
 FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4184.0
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 

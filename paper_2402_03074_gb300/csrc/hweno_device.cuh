@@ -73,12 +73,13 @@ __device__ __forceinline__ double mirror_sign(int c, int m, int fx, int fy) {
   return s;
 }
 
-// Reciprocal 1/x: Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
-// seeded with the single-precision reciprocal of x; two steps take the < 2^-22 relative error
-// of the seed below 2^-52 (result within 1 ulp of 1/x).  The double <-> float format changes
-// of the seed are done on the integer bits (x's significand truncated to 23 bits; the float
-// result widened exactly), so only the four FMAs use the FP64 pipe.  Values whose exponent is
-// outside +-100 of 1 (where the float seed could over- or underflow) use the division.
+// Reciprocal 1/x: the single-precision reciprocal of x refined by one third-order step of
+// Householder's iteration for 1/x, y <- y + y (e + e^2) with e = 1 - x y: the new residual is
+// 1 - x y (1 + e + e^2) = e^3, so the seed's < 2^-22 relative error drops below 2^-66, under
+// the final rounding (result within 1 ulp of 1/x).  The double <-> float format changes of the
+// seed are done on the integer bits (x's significand truncated to 23 bits; the float result
+// widened exactly), so only three FMAs use the FP64 pipe.  Values whose exponent is outside
+// +-100 of 1 (where the float seed could over- or underflow) use the division.
 __device__ __forceinline__ double rcp_nr(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int eb = (int)((b >> 52) & 0x7ff);
@@ -90,11 +91,9 @@ __device__ __forceinline__ double rcp_nr(double x) {
   const unsigned long long yb = (unsigned long long)(rf & 0x80000000u) << 32 |
                                 (unsigned long long)((rf >> 23 & 0xffu) - 127u + 1023u) << 52 |
                                 (unsigned long long)(rf & 0x7fffffu) << 29;
-  double y = __longlong_as_double((long long)yb);
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double y = __longlong_as_double((long long)yb);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // Format changes between float and double on the integer bits, for the FP32-bulk path, where
@@ -164,9 +163,9 @@ template <int NS>
 __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], double uave,
                                                   const KProblem& P, double& a0,
                                                   double (&b)[NS]) {
-  double s = 0.0;
+  double s = fabs(beta[0] - beta[1]);
 #pragma unroll
-  for (int m = 1; m < NS; ++m) s += fabs(beta[0] - beta[m]);
+  for (int m = 2; m < NS; ++m) s += fabs(beta[0] - beta[m]);
   s *= 1.0 / (double)(NS - 1);
   const double tau = s * s;
   const double ua = (P.wmode == 1) ? 1.0 : uave;
@@ -188,9 +187,11 @@ __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], doub
   for (int m = 0; m < NS; ++m)
     Dm[m] = (m == 0) ? suf[1] : ((m == NS - 1) ? pre[NS - 1] : pre[m] * suf[m + 1]);
   const double N0 = fma(tau, Dm[0], D);
-  double nsum = 0.0;
+  // sum_{m>0} (D + tau D_m) = (NS - 1) D + tau sum_{m>0} D_m
+  double dsum = Dm[1];
 #pragma unroll
-  for (int m = 1; m < NS; ++m) nsum += fma(tau, Dm[m], D);
+  for (int m = 2; m < NS; ++m) dsum += Dm[m];
+  const double nsum = fma(tau, dsum, (double)(NS - 1) * D);
   const double S = fma(g0, N0, P.glo * nsum);
   // exponent checks on the INT pipe: D and S must be normal and far from overflow
   const long long eD = (__double_as_longlong(D) >> 52) & 0x7ff;

@@ -73,8 +73,8 @@ int main() {
 """
 
 
-def test_newton_reciprocal_within_one_ulp_of_division():
-    """rcp_nr (Newton-Raphson refinement of the FP32 reciprocal, two steps) against CUDA's
+def test_refined_reciprocal_within_one_ulp_of_division():
+    """rcp_nr (the FP32 reciprocal refined by one third-order step) against CUDA's
     correctly rounded 1/x on 2^20 values over 2^-200 .. 2^200, both signs."""
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "rcp.cu")
