@@ -178,6 +178,15 @@ KProblem kproblem_of(const hweno_problem* p) {
   k.wmode = p->weights;
   k.glo = p->gamma_lo;
   k.eps = p->eps;
+  k.gm1 = k.gam - 1.0;
+  k.g0[0] = 1.0 - 2.0 * k.glo;
+  k.g0[1] = 1.0 - 4.0 * k.glo;
+  k.gamf = (float)k.gam;
+  k.gm1f = (float)k.gm1;
+  k.inv_dxf = (float)k.inv_dx;
+  k.inv_dyf = (float)k.inv_dy;
+  k.axf = (float)k.ax;
+  k.ayf = (float)k.ay;
   return k;
 }
 

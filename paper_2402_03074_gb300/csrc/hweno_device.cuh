@@ -20,7 +20,20 @@ struct KProblem {
   double ax, ay, gam;
   int wmode;          // 0 scale-invariant, 1 original (u_ave = 1)
   double glo, eps;    // linear weight of the low-degree polynomials, epsilon
+  // derived on the host once, so no kernel recomputes them per use:
+  double gm1;         // gam - 1
+  double g0[2];       // linear weight of the big-stencil polynomial, 1 - (NS - 1) glo, for
+                      // NS = 3 (1D) and NS = 5 (2D)
+  float gamf, gm1f, inv_dxf, inv_dyf, axf, ayf;  // FP32 copies for the FP32-bulk path
 };
+
+// A kernel constant in the bulk precision R: for float its FP32 copy, rounded on the host, so
+// the FP32-bulk path needs no double -> float conversion (an FP64-pipe instruction) per use.
+template <typename R>
+__device__ __forceinline__ R kconst(double d, float f) {
+  if constexpr (sizeof(R) == sizeof(float)) return f;
+  else return d;
+}
 
 // Pointers and scalars of one stage launch.
 struct KStage {
@@ -169,7 +182,7 @@ __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], doub
   s *= 1.0 / (double)(NS - 1);
   const double tau = s * s;
   const double ua = (P.wmode == 1) ? 1.0 : uave;
-  const double g0 = 1.0 - (double)(NS - 1) * P.glo;
+  const double g0 = P.g0[NS == 3 ? 0 : 1];
   double d[NS];
 #pragma unroll
   for (int m = 0; m < NS; ++m) d[m] = fma(beta[m], ua, P.eps);
@@ -478,7 +491,7 @@ template <typename R>
 struct Phys<EQ_ADV, R> {
   static constexpr int NC = 1;
   __device__ static void flux(const KProblem& P, int dir, const R* u, R* f) {
-    f[0] = (R)(dir == 0 ? P.ax : P.ay) * u[0];
+    f[0] = (dir == 0 ? kconst<R>(P.ax, P.axf) : kconst<R>(P.ay, P.ayf)) * u[0];
   }
   __device__ static double speed(const KProblem& P, int dir, const double* u) {
     return fabs(dir == 0 ? P.ax : P.ay);
@@ -494,7 +507,7 @@ struct Phys<EQ_BURG, R> {
 // Euler flux in direction dir for DIM = 1 (3 comps) or 2 (4 comps)
 template <int DIM, typename R>
 __device__ __forceinline__ void euler_flux(const KProblem& P, int dir, const R* u, R* f) {
-  const R gm1 = (R)(P.gam - 1.0);
+  const R gm1 = kconst<R>(P.gm1, P.gm1f);
   if (DIM == 1) {
     const R vel = u[1] * rcp<R>(u[0]);
     const R p = gm1 * (u[2] - R(0.5) * u[1] * vel);
@@ -524,11 +537,11 @@ __device__ __forceinline__ double euler_speed(const KProblem& P, int dir, const 
   const double ir = 1.0 / u[0];
   if (DIM == 1) {
     const double vel = u[1] * ir;
-    const double p = (P.gam - 1.0) * (u[2] - 0.5 * u[1] * vel);
+    const double p = P.gm1 * (u[2] - 0.5 * u[1] * vel);
     return fabs(vel) + sqrt(P.gam * p * ir);
   }
   const double vx = u[1] * ir, vy = u[2] * ir;
-  const double p = (P.gam - 1.0) * (u[3] - 0.5 * (u[1] * vx + u[2] * vy));
+  const double p = P.gm1 * (u[3] - 0.5 * (u[1] * vx + u[2] * vy));
   return fabs(dir == 0 ? vx : vy) + sqrt(P.gam * p * ir);
 }
 
@@ -542,7 +555,7 @@ __device__ __forceinline__ bool euler_speeds(const KProblem& P, const double* u,
   const double vy = DIM == 2 ? u[2] * ir : 0.0;
   const double e = u[DIM + 1] - 0.5 * (DIM == 2 ? fma(u[1], vx, u[2] * vy) : u[1] * vx);
   const bool ok = u[0] > 0.0 && e > 0.0 && finite_bits(e);
-  const double c = sqrt(P.gam * ((P.gam - 1.0) * e) * ir);
+  const double c = sqrt(P.gam * (P.gm1 * e) * ir);
   s0 = fabs(vx) + c;
   s1 = fabs(vy) + c;
   return ok;
@@ -557,9 +570,9 @@ struct Eig1 {
   __device__ __forceinline__ bool init(const KProblem& P, R rho, R m, R E) {
     const R ir = R(1) / rho;
     u = m * ir;
-    const R gm1 = (R)(P.gam - 1.0);
+    const R gm1 = kconst<R>(P.gm1, P.gm1f);
     const R p = gm1 * (E - R(0.5) * m * u);
-    const R c2 = (R)P.gam * p * ir;
+    const R c2 = kconst<R>(P.gam, P.gamf) * p * ir;
     c = sqrt(c2);
     H = (E + p) * ir;
     const R b1 = gm1 / c2;
@@ -598,10 +611,10 @@ struct Eig2 {
     const R vx = U[1] * ir, vy = U[2] * ir;
     un = d == 0 ? vx : vy;
     ut = d == 0 ? vy : vx;
-    const R gm1 = (R)(P.gam - 1.0);
+    const R gm1 = kconst<R>(P.gm1, P.gm1f);
     q2h = R(0.5) * (vx * vx + vy * vy);
     const R p = gm1 * (U[3] - U[0] * q2h);
-    const R c2 = (R)P.gam * p * ir;
+    const R c2 = kconst<R>(P.gam, P.gamf) * p * ir;
     const R rc = rsqrt(c2);       // 1/c; c and 1/c^2 follow from it
     c = c2 * rc;
     H = (U[3] + p) * ir;

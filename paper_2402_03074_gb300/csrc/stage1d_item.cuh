@@ -112,7 +112,7 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
   double wmax = 0.0;
   if (upd) {
     const double dt = *S.dt;
-    const R idx = (R)P.inv_dx;
+    const R idx = kconst<R>(P.inv_dx, P.inv_dxf);
     double outv[NC * NM];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {

@@ -90,7 +90,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   const bool outc = (t >= 1 && t <= wout && i < nx);
   const R a1 = (R)S.alpha_in[0], a2 = (R)S.alpha_in[1];
   const double dt = *S.dt;
-  const R idx = (R)P.inv_dx, idy = (R)P.inv_dy;
+  const R idx = kconst<R>(P.inv_dx, P.inv_dxf), idy = kconst<R>(P.inv_dy, P.inv_dyf);
   const R s15 = R(HW_S15);
 
   auto load_row = [&](int r) {
