@@ -328,14 +328,18 @@ def run_ours(args):
         pin = torch.empty(U0.shape, dtype=torch.float64, pin_memory=True).numpy()
         pin[...] = U0
         sid = H.hweno_open(eng, p64, pin)
-        H.hweno_step(eng, sid)
-        barrier()
-        t0 = time.perf_counter()
         tsim = 0.0
-        for _ in range(args.e2e_steps):
+
+        def e2e_step(tsim):
             H.hweno_set_state(eng, sid, pin, tsim)
             H.hweno_step(eng, sid)
-            _, tsim = H.hweno_get_state(eng, sid, pin)
+            return H.hweno_get_state(eng, sid, pin)[1]
+        tsim = e2e_step(tsim)   # untimed: the first pass through each entry point
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            tsim = e2e_step(tsim)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         H.hweno_close(eng, sid)
@@ -651,7 +655,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--kernel-reps", type=int, default=5)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-window", type=int, default=128)
     ap.add_argument("--no-mixed", action="store_true")
