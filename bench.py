@@ -352,7 +352,7 @@ def run_ours(args):
     if not args.no_served:
         budget = 150 * 10**9  # the served configuration's HBM admission budget
         served = served_stream(H, I, lambda: H.hweno_create(device=dev, hbm_budget_bytes=budget),
-                               args.served_m, 50.0,
+                               args.served_m, args.served_rate,
                                [int(g) for g in args.served_grids.split(",")],
                                args.served_tlo, args.served_thi, seed=rank)
     tubes = None
@@ -674,6 +674,8 @@ def main():
     ap.add_argument("--tubes-n", type=int, default=4000)
     ap.add_argument("--tubes-t", type=float, default=1.5)
     ap.add_argument("--served-m", type=int, default=16)
+    ap.add_argument("--served-rate", type=float, default=50.0,
+                    help="Poisson arrival rate of the served stream, requests/s")
     ap.add_argument("--served-grids", default="128,256,384,512")
     ap.add_argument("--served-tlo", type=float, default=0.02)
     ap.add_argument("--served-thi", type=float, default=0.05)
