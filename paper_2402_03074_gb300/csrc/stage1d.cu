@@ -1,9 +1,27 @@
 // stage1d.cu -- single-solve launch of the fused 1D HWENO-U stage (one block per BW-2 cells;
 // the block's work is in stage1d_item.cuh).
+//
+// Block width: a stage is FP64-pipe bound per SM, and an SM has one FP64 unit however many of
+// a grid's blocks it holds, so a short grid must be spread over as many SMs as possible.  The
+// 128-thread blocks (126 cells each) are used once they give every SM at least one block;
+// shorter grids take one-warp blocks of 30 cells (4000 cells: 134 blocks on 134 SMs instead of
+// 32 blocks on 32 SMs).
 #include "launch.h"
 #include "stage1d_item.cuh"
 
 namespace hw {
+
+static int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (cache[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = n > 0 ? n : 1;
+  }
+  return cache[dev];
+}
 
 template <int EQ, bool CHAR, typename R, int BW>
 __global__ void __launch_bounds__(BW) stage1d_kernel(KProblem P, KStage S) {
@@ -13,17 +31,21 @@ __global__ void __launch_bounds__(BW) stage1d_kernel(KProblem P, KStage S) {
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t launch1d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
-  constexpr int BW = 128;
-  const int blocks = (P.nx + (BW - 2) - 1) / (BW - 2);
-  stage1d_kernel<EQ, CHAR, R, BW><<<blocks, BW, 0, st>>>(P, S);
+  const int wide = (P.nx + 125) / 126;
+  if (wide >= sm_count()) {
+    stage1d_kernel<EQ, CHAR, R, 128><<<wide, 128, 0, st>>>(P, S);
+  } else {
+    stage1d_kernel<EQ, CHAR, R, 32><<<(P.nx + 29) / 30, 32, 0, st>>>(P, S);
+  }
   return cudaGetLastError();
 }
 
 template <int EQ, bool CHAR, typename R>
 static size_t local1d_t() {
-  cudaFuncAttributes fa;
+  cudaFuncAttributes fa, fb;
   if (cudaFuncGetAttributes(&fa, stage1d_kernel<EQ, CHAR, R, 128>) != cudaSuccess) return 0;
-  return fa.localSizeBytes;
+  if (cudaFuncGetAttributes(&fb, stage1d_kernel<EQ, CHAR, R, 32>) != cudaSuccess) return 0;
+  return fa.localSizeBytes > fb.localSizeBytes ? fa.localSizeBytes : fb.localSizeBytes;
 }
 
 cudaError_t prepare_stage1d(size_t* max_local) {

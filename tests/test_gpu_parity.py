@@ -75,8 +75,10 @@ def test_stage_2d_edge_sizes(nx, ny):
     _check_stage(op, hp, 2, seed=6)
 
 
-@pytest.mark.parametrize("n", [2, 3, 125, 126, 127, 253])
+@pytest.mark.parametrize("n", [2, 3, 29, 30, 31, 61, 125, 126, 127, 253, 40001])
 def test_stage_1d_edge_sizes(n):
+    """Short grids run in one-warp blocks of 30 cells (multiples and +-1 of that width); a grid
+    long enough to give every SM a 128-thread block (40001 cells) runs in those."""
     op, hp = problems(1, "euler", n, bc=1)
     _check_stage(op, hp, 3, seed=7)
 
