@@ -606,6 +606,56 @@ def run_paper_tables(args):
     H.hweno_destroy(eng)
 
 
+def run_dt_sweep(args):
+    """Time-step dependence of the paper's 2D accuracy examples (Tables 3.4-3.6), FP64: the
+    error against the exact solution of Example 3.3 (2D Burgers, T = 0.5/pi) at 40^2, 80^2,
+    120^2 and Example 3.4 (2D Euler density wave, T = 2) at 40^2, 80^2, for dt = c dx with
+    c in {0.1, 0.02, 0.005} and for the CFL 0.6 rule, with the scale-invariant weights (Eq.
+    2.22) and the linear weights; for Euler also the original weights and the component-wise
+    reconstruction.  One JSON line per run, beside the printed values."""
+    from paper_2402_03074_gb300 import build as B
+    B.build()
+    from paper_2402_03074_gb300 import _binding as H
+    from paper_2402_03074_gb300 import inputs as I
+    with open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")) as f:
+        tables = json.load(f)
+    eng = H.hweno_create()
+    variants = {"scale-invariant": (H.HWENO_W_SCALE_INVARIANT, 1),
+                "linear": (H.HWENO_W_LINEAR, 1),
+                "original": (H.HWENO_W_ORIGINAL, 1),
+                "scale-invariant, component-wise": (H.HWENO_W_SCALE_INVARIANT, 0)}
+    cases = [("Table 3.4, 2D Burgers", H.HWENO_BURGERS, n, I.burgers_sine_2d(n),
+              lambda n, t: I.burgers_exact_2d(n, t), "table_3_4_burgers_2d",
+              ("scale-invariant", "linear")) for n in (40, 80, 120)]
+    cases += [("Table 3.6, 2D Euler", H.HWENO_EULER, n, I.euler_density_wave_2d(n),
+               lambda n, t: I.euler_density_wave_exact_2d(n, t), "table_3_6_euler_2d",
+               tuple(variants)) for n in (40, 80)]
+    for name, eq, n, w, exact, key, names in cases:
+        ex = exact(n, w.t_end)
+        printed = tables[key].get(str(n))
+        for c in ("cfl0.6", 0.1, 0.02, 0.005):
+            for vname in names:
+                wm, ch = variants[vname]
+                p = H.make_problem(dim=2, equation=eq, nx=n, ny=n, x0=w.x0, x1=w.x1, y0=w.y0,
+                                   y1=w.y1, bc=w.bc, cfl=0.6, weights=wm, characteristic=ch,
+                                   dt_fixed=0.0 if c == "cfl0.6" else c * (w.x1 - w.x0) / n)
+                sid = H.hweno_open(eng, p, w.U0)
+                steps = H.hweno_advance(eng, sid, w.t_end)
+                out, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+                H.hweno_close(eng, sid)
+                e = np.abs(out[0, 0] - ex[0, 0])
+                rec = {"case": name, "mesh": n, "dt": c if c == "cfl0.6" else f"{c} dx",
+                       "weights": vname, "steps": steps, "l1": float(e.mean()),
+                       "linf": float(e.max()), "paper_l1": printed["l1"],
+                       "paper_linf": printed["linf"]}
+                if eq == H.HWENO_BURGERS:
+                    ev = np.abs(out[0, 1] - ex[0, 1])
+                    rec["first_moment_l1"] = float(ev.mean())
+                    rec["first_moment_linf"] = float(ev.max())
+                print(json.dumps(rec), flush=True)
+    H.hweno_destroy(eng)
+
+
 def run_sweep(args):
     """Convergence of the FP64 and FP32-bulk paths on the periodic isentropic vortex
     (rho = p = 1, u = v = 1 plus the vortex, [0,1]^2, T = 0.05) against the exact translated
@@ -680,6 +730,8 @@ def main():
     ap.add_argument("--served-tlo", type=float, default=0.02)
     ap.add_argument("--served-thi", type=float, default=0.05)
     ap.add_argument("--sweep", action="store_true", help="precision / convergence study")
+    ap.add_argument("--dt-sweep", action="store_true",
+                    help="time-step dependence of the 2D accuracy examples (Tables 3.4-3.6)")
     ap.add_argument("--paper-tables", action="store_true",
                     help="the paper's accuracy examples at 240 cells per direction")
     ap.add_argument("--sweep-sizes", default="128,256,512,1024,2048")
@@ -689,6 +741,8 @@ def main():
         args.warmup = 3
     if args.sweep:
         run_sweep(args)
+    elif args.dt_sweep:
+        run_dt_sweep(args)
     elif args.paper_tables:
         run_paper_tables(args)
     elif args.impl == "reference":

@@ -61,9 +61,11 @@ extern "C" {
 #define HWENO_FP64 0
 #define HWENO_MIXED32 1
 /* nonlinear weights: scale-invariant (Eq. 2.11 / 2.22) or the original ones with
-   u_ave = 1 (the Remark after Eq. 2.11) */
+   u_ave = 1 (the Remark after Eq. 2.11); HWENO_W_LINEAR replaces them by the linear weights
+   (omega = gamma: the linear scheme of Sec. 2.3), for accuracy and stability studies */
 #define HWENO_W_SCALE_INVARIANT 0
 #define HWENO_W_ORIGINAL 1
+#define HWENO_W_LINEAR 2
 
 /* A problem u_t + f(u)_x (+ g(u)_y) = 0 on [x0,x1] (x [y0,y1]) (Sec. 2.1, 2.2). */
 typedef struct hweno_problem {
@@ -79,7 +81,7 @@ typedef struct hweno_problem {
   double t_end;       /* end time used by hweno_submit */
   int precision;      /* HWENO_FP64 | HWENO_MIXED32 */
   int characteristic; /* Euler: 1 = local characteristic decomposition (Remark 2.2) */
-  int weights;        /* HWENO_W_SCALE_INVARIANT | HWENO_W_ORIGINAL */
+  int weights;        /* HWENO_W_SCALE_INVARIANT | HWENO_W_ORIGINAL | HWENO_W_LINEAR */
   double gamma_lo;    /* linear weight of each low-degree polynomial (1/400, Sec. 3) */
   double eps;         /* epsilon of the nonlinear weights (1e-10, Eq. 2.11); must be > 0 */
 } hweno_problem;

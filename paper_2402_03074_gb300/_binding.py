@@ -20,7 +20,7 @@ HWENO_ERR_BUSY, HWENO_ERR_TIMEOUT, HWENO_ERR_STATE = -5, -6, -7
 HWENO_ADVECTION, HWENO_BURGERS, HWENO_EULER = 0, 1, 2
 HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE = 0, 1, 2
 HWENO_FP64, HWENO_MIXED32 = 0, 1
-HWENO_W_SCALE_INVARIANT, HWENO_W_ORIGINAL = 0, 1
+HWENO_W_SCALE_INVARIANT, HWENO_W_ORIGINAL, HWENO_W_LINEAR = 0, 1, 2
 
 _NAMES = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
           -4: "ERR_NONPHYSICAL", -5: "ERR_BUSY", -6: "ERR_TIMEOUT", -7: "ERR_STATE"}

@@ -148,7 +148,8 @@ int problem_check(const hweno_problem* p, std::string* why) {
       return bad("2D cells must be square (dx == dy): Eq. 2.20 assumes it");
   }
   if (p->precision != HWENO_FP64 && p->precision != HWENO_MIXED32) return bad("unknown precision");
-  if (p->weights != HWENO_W_SCALE_INVARIANT && p->weights != HWENO_W_ORIGINAL)
+  if (p->weights != HWENO_W_SCALE_INVARIANT && p->weights != HWENO_W_ORIGINAL &&
+      p->weights != HWENO_W_LINEAR)
     return bad("unknown weights");
   const double gmax = p->dim == 1 ? 0.5 : 0.25;
   if (!(p->gamma_lo > 0.0 && p->gamma_lo < gmax)) return bad("gamma_lo out of range");

@@ -18,7 +18,7 @@ struct KProblem {
   double dx, dy, inv_dx, inv_dy;
   int bc[4];
   double ax, ay, gam;
-  int wmode;          // 0 scale-invariant, 1 original (u_ave = 1)
+  int wmode;          // 0 scale-invariant, 1 original (u_ave = 1), 2 linear (omega = gamma)
   double glo, eps;    // linear weight of the low-degree polynomials, epsilon
   // derived on the host once, so no kernel recomputes them per use:
   double gm1;         // gam - 1
@@ -176,6 +176,12 @@ template <int NS>
 __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], double uave,
                                                   const KProblem& P, double& a0,
                                                   double (&b)[NS]) {
+  if (P.wmode == 2) {   // linear weights (omega = gamma): the combined polynomial is p_0
+    a0 = 1.0;
+#pragma unroll
+    for (int m = 0; m < NS; ++m) b[m] = 0.0;
+    return;
+  }
   double s = fabs(beta[0] - beta[1]);
 #pragma unroll
   for (int m = 2; m < NS; ++m) s += fabs(beta[0] - beta[m]);

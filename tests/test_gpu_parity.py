@@ -90,6 +90,15 @@ def test_weights_original_variant():
     _check_stage(op, hp, 2, seed=9)
 
 
+def test_weights_linear_variant():
+    """HWENO_W_LINEAR (omega = gamma, the linear scheme of Sec. 2.3) against the oracle's
+    linear-weight mode, 1D and 2D."""
+    op, hp = problems(2, "euler", 70, 33, bc=1, weights=2)
+    _check_stage(op, hp, 1, seed=18)
+    op, hp = problems(1, "euler", 150, bc=0, weights=2)
+    _check_stage(op, hp, 2, seed=19)
+
+
 def _oracle_of(hp):
     eq = {H.HWENO_ADVECTION: O.ADVECTION, H.HWENO_BURGERS: O.BURGERS, H.HWENO_EULER: O.EULER}[hp.equation]
     return O.Problem(dim=hp.dim, eq=eq, nx=hp.nx, ny=hp.ny, x0=hp.x0, x1=hp.x1, y0=hp.y0, y1=hp.y1,

@@ -278,6 +278,31 @@ def test_2d_burgers_converges_to_the_characteristic_solution():
     assert np.log2(si[0, 0] / si[1, 0]) > 3.0, si
 
 
+@pytest.mark.parametrize("n,tol_l1,tol_linf", [(40, 0.2, 0.1), (80, 0.2, 0.15)])
+def test_2d_burgers_matches_table_3_4_and_3_5(n, tol_l1, tol_linf):
+    """Example 3.3 with the scale-invariant weights against Table 3.4 (cell averages) and, at
+    40^2, Table 3.5 (first moments).  The paper does not state its time step; with
+    dt = 0.02 dx the printed values are reproduced (L1 within 20 %, Linf within 10-15 %).
+    The weights' response to smooth data decides these coarse-mesh errors (the linear
+    weights give a 40x smaller error at 40^2), so Step 3 is pinned by printed numbers here:
+    tau with the divisor 2 instead of 4 misses Table 3.4 by 2x-4x."""
+    g = _golden()["table_3_4_burgers_2d"][str(n)]
+    gv = _golden()["table_3_5_burgers_2d_first_moments"][str(n)]
+    w = I.burgers_sine_2d(n)
+    ex = I.burgers_exact_2d(n, w.t_end)
+    P = O.Problem(dim=2, eq=O.BURGERS, nx=n, ny=n, x0=0.0, x1=4.0, y0=0.0, y1=4.0)
+    U, t, _, st = O.run(P, w.U0, 0.0, w.t_end, dt_fixed=0.02 * 4.0 / n)
+    assert st == 0 and t == w.t_end
+    e, ev, ew = (np.abs(U[0, m] - ex[0, m]) for m in range(3))
+    assert e.mean() == pytest.approx(g["l1"], rel=tol_l1)
+    assert e.max() == pytest.approx(g["linf"], rel=tol_linf)
+    # the solution depends on x + y only: the two first moments are equal (Table 3.5 note)
+    np.testing.assert_allclose(U[0, 1], U[0, 2], rtol=0, atol=1e-12)
+    if n == 40:
+        assert ev.mean() == pytest.approx(gv["l1"], rel=0.1)
+        assert ev.max() == pytest.approx(gv["linf"], rel=0.1)
+
+
 def _run_example(w):
     P = O.Problem(dim=1, eq=O.EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
     U, t, ns, st = O.run(P, w.U0, 0.0, w.t_end)
