@@ -223,6 +223,16 @@ int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* mome
 int hweno_tuning_save(const char* path);
 int hweno_tuning_load(const char* path);
 
+/* ---------------------------------------------------------------------------------------
+ * Measurement utility (no counterpart in the paper).  The FMA throughput of device
+ * `device` in FP64 (fp64 = 1) or FP32 (fp64 = 0), from one kernel of independent FMA chains
+ * over every SM (eight 256-thread blocks per SM, eight chains per thread): *flop_per_s =
+ * 2 x FMAs per second, the best of five timed launches after one untimed one (about 10 ms
+ * each).  These are the ALU peaks against which the stage kernels' rooflines are stated.
+ * Allocates and frees a few kilobytes of device memory; synchronises the device.
+ * --------------------------------------------------------------------------------------- */
+int hweno_fma_peak(int device, int fp64, double* flop_per_s);
+
 #ifdef __cplusplus
 }
 #endif

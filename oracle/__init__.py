@@ -26,17 +26,33 @@ W_SCALE_INVARIANT, W_ORIGINAL, W_LINEAR = 0, 1, 2
 RK_MODIFIED, RK_PLAIN = 0, 1
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (FP contraction off: plain IEEE binary64 rounding)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(os.path.join(_HERE, "hweno_oracle.h"))):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def _compile(target: str, openmp: bool) -> None:
+    tmp = target + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
+    os.replace(tmp, target)
+
+
+def _current(target: str) -> bool:
+    return (os.path.exists(target) and os.path.getmtime(target) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(target) >= os.path.getmtime(os.path.join(_HERE, "hweno_oracle.h")))
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (FP contraction off: plain IEEE binary64 rounding), and
+    liboracle_omp.so, the same source with its per-cell stage loops shared by OpenMP threads
+    (when the compiler has OpenMP; otherwise that library is the serial one)."""
+    if force or not _current(_LIB):
+        _compile(_LIB, False)
+    if force or not _current(_LIB_OMP):
+        try:
+            _compile(_LIB_OMP, True)
+        except subprocess.CalledProcessError:
+            _compile(_LIB_OMP, False)
     return _LIB
 
 
@@ -52,35 +68,54 @@ class _Problem(ctypes.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
-def lib():
-    global _lib
+def lib(threads: int = 0):
+    """The serial oracle (threads = 0), or the OpenMP build set to `threads` threads."""
+    global _lib, _lib_omp
+    if threads > 0:
+        if _lib_omp is None:
+            build()
+            _lib_omp = _declare(ctypes.CDLL(_LIB_OMP))
+        _lib_omp.orc_set_threads(threads)
+        return _lib_omp
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        P = ctypes.POINTER(_Problem)
-        dp = ctypes.POINTER(ctypes.c_double)
-        i64p = ctypes.POINTER(ctypes.c_int64)
-        L.orc_recon1d.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_recon1d.restype = None
-        L.orc_recon2d.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_recon2d.restype = None
-        L.orc_eigen.argtypes = [P, dp, ctypes.c_int, dp, dp]
-        L.orc_eigen.restype = ctypes.c_int
-        L.orc_alpha.argtypes = [P, dp, dp]
-        L.orc_alpha.restype = None
-        L.orc_stage.argtypes = [P, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp]
-        L.orc_stage.restype = ctypes.c_int
-        L.orc_stage_cells.argtypes = [P, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double,
-                                      ctypes.c_int64, i64p, dp, dp]
-        L.orc_stage_cells.restype = ctypes.c_int
-        L.orc_step.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_step.restype = ctypes.c_int
-        L.orc_run.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int64, ctypes.c_double, i64p]
-        L.orc_run.restype = ctypes.c_int
-        _lib = L
+        _lib = _declare(ctypes.CDLL(_LIB))
     return _lib
+
+
+def threads_available(threads: int) -> int:
+    """Threads the OpenMP build will use when asked for `threads` (1 without OpenMP)."""
+    return lib(threads).orc_set_threads(threads)
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C functions."""
+    P = ctypes.POINTER(_Problem)
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.orc_recon1d.argtypes = [dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_recon1d.restype = None
+    L.orc_recon2d.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_recon2d.restype = None
+    L.orc_eigen.argtypes = [P, dp, ctypes.c_int, dp, dp]
+    L.orc_eigen.restype = ctypes.c_int
+    L.orc_alpha.argtypes = [P, dp, dp]
+    L.orc_alpha.restype = None
+    L.orc_stage.argtypes = [P, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double, dp]
+    L.orc_stage.restype = ctypes.c_int
+    L.orc_stage_cells.argtypes = [P, ctypes.c_int, dp, dp, dp, dp, ctypes.c_double,
+                                  ctypes.c_int64, i64p, dp, dp]
+    L.orc_stage_cells.restype = ctypes.c_int
+    L.orc_step.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_step.restype = ctypes.c_int
+    L.orc_run.argtypes = [P, dp, dp, ctypes.c_double, ctypes.c_int64, ctypes.c_double, i64p]
+    L.orc_run.restype = ctypes.c_int
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    L.orc_set_threads.restype = ctypes.c_int
+    return L
 
 
 def _dp(a):
@@ -178,8 +213,9 @@ def alpha(prob: Problem, U: np.ndarray) -> np.ndarray:
     return a
 
 
-def stage(prob: Problem, k: int, Uin, Un, Vh, alpha_in, dt):
-    """One stage of Eq. 2.13; returns (Uout, Vh, status). Vh is filled when k == 1."""
+def stage(prob: Problem, k: int, Uin, Un, Vh, alpha_in, dt, threads: int = 0):
+    """One stage of Eq. 2.13; returns (Uout, Vh, status). Vh is filled when k == 1.
+    threads > 0: the OpenMP build with that many threads (bitwise the same result)."""
     Uin = np.ascontiguousarray(Uin, dtype=np.float64)
     Un = np.ascontiguousarray(Un, dtype=np.float64)
     if Vh is None:
@@ -188,7 +224,8 @@ def stage(prob: Problem, k: int, Uin, Un, Vh, alpha_in, dt):
     Uout = np.zeros(prob.shape)
     a = np.ascontiguousarray(alpha_in, dtype=np.float64)
     pc = prob.c()
-    st = lib().orc_stage(ctypes.byref(pc), k, _dp(Uin), _dp(Un), _dp(Vh), _dp(a), dt, _dp(Uout))
+    st = lib(threads).orc_stage(ctypes.byref(pc), k, _dp(Uin), _dp(Un), _dp(Vh), _dp(a), dt,
+                                _dp(Uout))
     return Uout, Vh, st
 
 
@@ -210,23 +247,80 @@ def stage_cells(prob: Problem, k: int, Uin, Un, Vh, alpha_in, dt, cells):
     return out, vho, st
 
 
-def step(prob: Problem, U, t=0.0, t_end=float("inf"), dt_fixed=0.0):
+def step(prob: Problem, U, t=0.0, t_end=float("inf"), dt_fixed=0.0, threads: int = 0):
     """One time step (in a copy); returns (U, t, dt, status)."""
     U = np.ascontiguousarray(U, dtype=np.float64).copy()
     tt = ctypes.c_double(t)
     dt = ctypes.c_double(0.0)
     pc = prob.c()
-    st = lib().orc_step(ctypes.byref(pc), _dp(U), ctypes.byref(tt), t_end, dt_fixed,
-                        ctypes.byref(dt))
+    st = lib(threads).orc_step(ctypes.byref(pc), _dp(U), ctypes.byref(tt), t_end, dt_fixed,
+                               ctypes.byref(dt))
     return U, tt.value, dt.value, st
 
 
-def run(prob: Problem, U, t=0.0, t_end=float("inf"), max_steps=-1, dt_fixed=0.0):
-    """Steps until t_end or max_steps; returns (U, t, steps, status)."""
+def run(prob: Problem, U, t=0.0, t_end=float("inf"), max_steps=-1, dt_fixed=0.0,
+        threads: int = 0):
+    """Steps until t_end or max_steps; returns (U, t, steps, status).  threads > 0: the
+    OpenMP build with that many threads (bitwise the same result as the serial one)."""
     U = np.ascontiguousarray(U, dtype=np.float64).copy()
     tt = ctypes.c_double(t)
     ns = ctypes.c_int64(0)
     pc = prob.c()
-    st = lib().orc_run(ctypes.byref(pc), _dp(U), ctypes.byref(tt), t_end, max_steps, dt_fixed,
-                       ctypes.byref(ns))
+    st = lib(threads).orc_run(ctypes.byref(pc), _dp(U), ctypes.byref(tt), t_end, max_steps,
+                              dt_fixed, ctypes.byref(ns))
     return U, tt.value, ns.value, st
+
+
+# ------------------------------------------------------------------------------------------
+# floating-point operation count of one stage (flop_count.cpp: the oracle's source compiled
+# with a counting scalar)
+# ------------------------------------------------------------------------------------------
+_FLOP_SRC = os.path.join(_HERE, "flop_count.cpp")
+_FLOP_LIB = os.path.join(_HERE, "libflopcount.so")
+_flop = None
+
+
+def build_flop_count(force: bool = False) -> str:
+    deps = (_FLOP_SRC, _SRC, os.path.join(_HERE, "hweno_oracle.h"))
+    if (not force and os.path.exists(_FLOP_LIB)
+            and all(os.path.getmtime(_FLOP_LIB) >= os.path.getmtime(d) for d in deps)):
+        return _FLOP_LIB
+    tmp = _FLOP_LIB + f".tmp{os.getpid()}"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                    tmp, _FLOP_SRC], check=True, cwd=_HERE)
+    os.replace(tmp, _FLOP_LIB)
+    return _FLOP_LIB
+
+
+FLOP_KINDS = ("add", "sub", "mul", "div", "sqrt", "total")
+
+
+def count_stage_flops(prob: Problem, k: int, Uin, Un=None, Vh=None, alpha_in=None, dt=1e-3):
+    """Floating-point operations of one oracle stage on the given data.  Returns a dict:
+    'dataflow' -- the distinct data-dependent operations (add, sub, mul, div, sqrt, total)
+    on which a stage output depends, after merging repeated identical operations and the
+    identities x*1, x*0, x+0, x-0, x/1; 'executed' -- every data-dependent operation the
+    oracle executes; 'wave_speeds' -- the executed operations of the LF speeds of all cells
+    of the output (the next stage's alpha).  Comparisons, negations and |x| are not counted."""
+    global _flop
+    if _flop is None:
+        build_flop_count()
+        L = ctypes.CDLL(_FLOP_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_count_stage_flops.argtypes = [ctypes.POINTER(_Problem), ctypes.c_int, dp, dp, dp,
+                                            dp, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+        L.orc_count_stage_flops.restype = ctypes.c_int
+        _flop = L
+    Uin = np.ascontiguousarray(Uin, dtype=np.float64)
+    Un = Uin if Un is None else np.ascontiguousarray(Un, dtype=np.float64)
+    if Vh is None:
+        Vh = np.zeros((prob.ncomp, prob.nmom - 1, prob.ny, prob.nx))
+    Vh = np.ascontiguousarray(Vh, dtype=np.float64)
+    a = alpha(prob, Uin) if alpha_in is None else np.ascontiguousarray(alpha_in, dtype=np.float64)
+    counts = (ctypes.c_int64 * 18)()
+    pc = prob.c()
+    st = _flop.orc_count_stage_flops(ctypes.byref(pc), k, _dp(Uin), _dp(Un), _dp(Vh), _dp(a), dt,
+                                     counts)
+    c = list(counts)
+    return {"dataflow": dict(zip(FLOP_KINDS, c[0:6])), "executed": dict(zip(FLOP_KINDS, c[6:12])),
+            "wave_speeds": dict(zip(FLOP_KINDS, c[12:18])), "status": st}

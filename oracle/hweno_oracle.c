@@ -28,6 +28,10 @@
  *   - transmissive boundaries copy the nearest interior cell's moments (index clamp);
  *     reflective boundaries mirror the cell, negating the normal momentum and every
  *     first moment in the normal direction (except that of the normal momentum).
+ * Threads: built with -fopenmp, the per-cell loops of a stage (reconstruction of every cell,
+ * face fluxes, updates) are shared by the threads row by row (cell by cell in 1D).  Each
+ * cell's arithmetic is the same in either build, so the results are bitwise identical; the
+ * serial build (no -fopenmp) ignores the pragmas.
  */
 #include "hweno_oracle.h"
 
@@ -36,6 +40,20 @@
 #include <string.h>
 
 #define NCMAX 4
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 int orc_ncomp(const orc_problem* P) {
   if (P->eq == ORC_EULER) return P->dim == 1 ? 3 : 4;
@@ -793,11 +811,14 @@ static int stage1d(const orc_problem* P, int k, const double* Uin, const double*
   cell1d* rc = (cell1d*)malloc(sizeof(cell1d) * (size_t)(n + 2)); /* cells -1..n */
   double* fh = (double*)malloc(sizeof(double) * NCMAX * (size_t)(n + 1)); /* faces 1/2.. */
   if (!rc || !fh) { free(rc); free(fh); return -1; }
+#pragma omp parallel for schedule(static)
   for (int i = -1; i <= n; ++i) recon_cell1d(P, Uin, i, &rc[i + 1]);
   /* face i+1/2 between cells i and i+1, i = -1..n-1 */
+#pragma omp parallel for schedule(static)
   for (int i = -1; i < n; ++i)
     lf_flux(P, 0, rc[i + 1].pt[3], rc[i + 2].pt[0], alpha[0], &fh[(size_t)(i + 1) * NCMAX]);
   int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (int i = 0; i < n; ++i) {
     double out[2 * NCMAX], vho[NCMAX];
     bad |= update_cell1d(P, k, i, &rc[i + 1], &fh[(size_t)i * NCMAX],
@@ -821,6 +842,7 @@ static int stage2d(const orc_problem* P, int k, const double* Uin, const double*
   const int64_t ex = nx + 2, ey = ny + 2; /* cells -1..nx, -1..ny */
   cell2d* rc = (cell2d*)malloc(sizeof(cell2d) * (size_t)(ex * ey));
   if (!rc) return -1;
+#pragma omp parallel for schedule(dynamic, 1)
   for (int j = -1; j <= ny; ++j)
     for (int i = -1; i <= nx; ++i) {
       int corner = (i < 0 || i >= nx) && (j < 0 || j >= ny);
@@ -828,6 +850,7 @@ static int stage2d(const orc_problem* P, int k, const double* Uin, const double*
     }
 #define RC(i, j) (&rc[((j) + 1) * ex + ((i) + 1)])
   int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       double fL[3][NCMAX], fR[3][NCMAX], gB[3][NCMAX], gT[3][NCMAX];

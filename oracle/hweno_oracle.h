@@ -52,6 +52,10 @@ typedef struct {
   double cfl;          /* CFL number (0.6 in Sec. 3) */
 } orc_problem;
 
+/* Threads of the per-cell stage loops in a -fopenmp build (liboracle_omp.so); returns the
+   number that will be used (1 in the serial build, which ignores n). */
+int orc_set_threads(int n);
+
 int orc_ncomp(const orc_problem* P);
 int orc_nmom(const orc_problem* P);
 
@@ -97,8 +101,8 @@ int orc_stage_cells(const orc_problem* P, int k, const double* Uin, const double
                     const double* Vh, const double alpha[2], double dt, int64_t ncells,
                     const int64_t* cells, double* out, double* vh_out);
 
-/* One full time step in place.  dt_fixed > 0 gives the step, else dt = CFL rule (R8
-   reading: cfl*dx/alpha in 1D, cfl/(alpha1/dx + alpha2/dy) in 2D), clipped to t_end-t. */
+/* One full time step in place.  dt_fixed > 0 gives the step, else dt = CFL rule (the
+   reading taken: cfl*dx/alpha in 1D, cfl/(alpha1/dx + alpha2/dy) in 2D), clipped to t_end-t. */
 int orc_step(const orc_problem* P, double* U, double* t, double t_end, double dt_fixed,
              double* dt_taken);
 

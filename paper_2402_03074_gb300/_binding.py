@@ -113,6 +113,7 @@ def lib() -> ctypes.CDLL:
                                           vp, vp, vp], ctypes.c_int),
             "hweno_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
             "hweno_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
+            "hweno_fma_peak": ([ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -274,6 +275,13 @@ def hweno_tuning_save(path: str) -> None:
 
 def hweno_tuning_load(path: str) -> int:
     return _check(lib().hweno_tuning_load(path.encode()))
+
+
+def hweno_fma_peak(device: int = 0, fp64: bool = True) -> float:
+    """FMA throughput of the device in flop/s (FMA = 2 flops), FP64 or FP32."""
+    r = ctypes.c_double()
+    _check(lib().hweno_fma_peak(device, 1 if fp64 else 0, ctypes.byref(r)))
+    return r.value
 
 
 HWENO_STATIC_BATCH_MAX = 16

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhweno.so")
 SOURCES = ["stage1d.cu", "stage2d.cu", "batch.cu", "engine.cu", "server.cu", "tune.cu",
-           "static_batch.cu"]
+           "static_batch.cu", "peaks.cu"]
 HEADERS = ["hweno_device.cuh", "launch.h", "server.h", "batch.h", "geometry.h",
            "stage1d_item.cuh", "stage2d_item.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
