@@ -35,6 +35,10 @@
 extern "C" {
 #endif
 
+/* bits of the device status word of a stage (hweno_stage_device, hweno_stage_batch_static) */
+#define HWENO_STATUS_NONPHYSICAL 1u
+#define HWENO_STATUS_DIRECT_WEIGHTS 2u
+
 /* status codes */
 #define HWENO_OK 0
 #define HWENO_PENDING 1
@@ -163,14 +167,28 @@ int hweno_poll(hweno_engine* eng, uint64_t ticket, double* moments_out, hweno_re
    engine has no server thread).  *active receives the number of live solves. */
 int hweno_serve(hweno_engine* eng, int64_t max_steps, int* active);
 
+/* Bound on how long a call of this engine waits for the device: hweno_step, hweno_advance,
+   hweno_conservation and hweno_serve return HWENO_ERR_TIMEOUT when a wait of theirs is not
+   over after `seconds` (0, the default: no bound).  Nothing queued is cancelled: it completes
+   on its own.  A call that times out may have stopped before queueing all of its own work
+   (its first wait reads back the solve's time and step count, behind whatever the stream
+   still holds), so the steps it took are those hweno_get_state shows afterwards.  Calls that
+   copy to or from a caller's host buffer (hweno_open, hweno_set_state, hweno_get_state,
+   hweno_submit, hweno_poll) always wait for that copy to finish.  HWENO_ERR_ARG for a
+   negative or NaN limit. */
+int hweno_set_wait_limit(hweno_engine* eng, double seconds);
+
 /* ---- one stage on caller-owned device buffers (Eq. 2.13, stage k = 1, 2, 3) ---------- */
 /* U_in: stage input, U_n: base state U^n, Vh: first-moment modifications of U^n
    (NC*(NM-1) arrays of ny*nx doubles; written when k == 1, read when k > 1), U_out: output
    (may alias U_n, not U_in).  All device pointers, host layout, double.  alpha_in: 2
    device doubles (LF speeds of U_in per direction); alpha_out: 2 device doubles that the
    stage raises (atomic max) to the wave speeds of U_out; dt: 1 device double; status: 1
-   device uint32 OR-ed with 1 if U_out is not physical.  stream: cudaStream_t (NULL:
-   legacy default stream).  Asynchronous; returns HWENO_ERR_ARG / HWENO_ERR_CUDA on a bad
+   device uint32 OR-ed with HWENO_STATUS_NONPHYSICAL if U_out is not physical, and (2D, for
+   information only) with HWENO_STATUS_DIRECT_WEIGHTS if some cell's nonlinear weights needed
+   the direct formula of Eq. 2.22 instead of the product form (data scaled by about 2^+-50 or
+   more; the results are the same up to rounding).  stream: cudaStream_t (NULL: legacy
+   default stream).  Asynchronous; returns HWENO_ERR_ARG / HWENO_ERR_CUDA on a bad
    problem or a launch failure. */
 int hweno_stage_device(const hweno_problem* p, int k, const double* U_in, const double* U_n,
                        double* Vh, double* U_out, const double* alpha_in, double* alpha_out,
@@ -190,15 +208,18 @@ int hweno_alpha_device(const hweno_problem* p, const double* U, double* alpha_ou
    holds it until the process exits) instead of allocated scratch.  No cudaMalloc, cudaFree
    or other allocating call is made.  The arrays are host arrays of n entries: problems, and
    per solve the same device buffers as hweno_stage_device (U_out[s] may alias U_n[s], not
-   U_in[s]).  Every call overwrites the static array, so calls whose work overlaps on the
-   GPU (other streams, other host threads) race on it; calls on one stream are ordered.  The
-   first call on a device sets up that device (looks up the array's device address and the
-   launch configuration), and should come before any stream capture.  Returns
+   U_in[s]); the buffers of different solves must not overlap (the same pointer in two
+   solves' U_out / U_in / U_n / Vh slots is rejected with HWENO_ERR_ARG; a partial overlap is
+   not detected, and races).  Every call overwrites the static array, so calls whose work
+   overlaps on the GPU (other streams, other host threads) race on it; calls on one stream
+   are ordered.  The first call on a device sets up that device (looks up the array's device
+   address and the launch configuration), and should come before any stream capture.  Returns
    HWENO_ERR_ARG for n < 1 or n > HWENO_STATIC_BATCH_MAX, a non-2D or invalid problem, mixed
    problem classes or a NULL pointer; HWENO_ERR_STATE if the context's per-thread stack limit
-   is below the kernel's stack frame (hweno_create and hweno_stage_device raise it; this
-   entry point does not, because raising it can allocate); HWENO_ERR_CUDA on a launch error.
-   Asynchronous on stream (NULL: the legacy default stream). */
+   (cudaLimitStackSize) is below the kernel's stack frame -- under 1 KB in this version, so the
+   CUDA default of 1 KB suffices; a caller that lowered the limit must give it back (this
+   entry point does not raise it, because raising it can allocate); HWENO_ERR_CUDA on a
+   launch error.  Asynchronous on stream (NULL: the legacy default stream). */
 #define HWENO_STATIC_BATCH_MAX 16
 int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
                              const double* const* U_in, const double* const* U_n,
@@ -213,9 +234,13 @@ int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
    (the widest bands of at most 126 columns, and 1.25, 1.5 and 2 times as many) -- keep the
    fastest in the process-wide tuning table (keyed by equation, characteristic decomposition,
    precision and grid) for every later single-solve launch of such problems, and report it
-   (*best_rows, *best_bands: 0 = the default; *best_ms: one stage).  Output pointers may be
-   NULL.  The tile shape changes no result bit (every cell and face is computed by the same
-   code in any decomposition). */
+   (*best_rows, *best_bands: 0 = the default; *best_ms: one stage).  For a 1D problem the
+   candidates are the block width (128 or 32 threads) and the threads per cell (one per cell,
+   or -- Euler with the characteristic decomposition -- one lane per characteristic field in
+   blocks of 128, 64 or 32 threads); *best_rows receives the block width and *best_bands the
+   threads per cell (1 or 4).  Output pointers may be NULL.  The 2D tile shape changes no
+   result bit (every cell and face is computed by the same code in any decomposition); the
+   1D lanes-per-field layout computes the same formulas, equal within rounding. */
 int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* moments_host,
                    int* best_rows, int* best_bands, double* best_ms);
 /* Save the tuning table as text (one entry per line, with the GPU name); load it back

@@ -21,6 +21,7 @@ HWENO_ADVECTION, HWENO_BURGERS, HWENO_EULER = 0, 1, 2
 HWENO_BC_PERIODIC, HWENO_BC_TRANSMISSIVE, HWENO_BC_REFLECTIVE = 0, 1, 2
 HWENO_FP64, HWENO_MIXED32 = 0, 1
 HWENO_W_SCALE_INVARIANT, HWENO_W_ORIGINAL, HWENO_W_LINEAR = 0, 1, 2
+HWENO_STATUS_NONPHYSICAL, HWENO_STATUS_DIRECT_WEIGHTS = 1, 2
 
 _NAMES = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
           -4: "ERR_NONPHYSICAL", -5: "ERR_BUSY", -6: "ERR_TIMEOUT", -7: "ERR_STATE"}
@@ -114,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "hweno_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
             "hweno_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
             "hweno_fma_peak": ([ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
+            "hweno_set_wait_limit": ([E, ctypes.c_double], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -275,6 +277,11 @@ def hweno_tuning_save(path: str) -> None:
 
 def hweno_tuning_load(path: str) -> int:
     return _check(lib().hweno_tuning_load(path.encode()))
+
+
+def hweno_set_wait_limit(eng, seconds: float) -> None:
+    """Bound the engine's waits for the device (0: no bound); HWENO_ERR_TIMEOUT past it."""
+    _check(lib().hweno_set_wait_limit(eng, seconds), eng)
 
 
 def hweno_fma_peak(device: int = 0, fp64: bool = True) -> float:

@@ -331,6 +331,7 @@ struct hweno_engine {
   uint64_t used = 0;
   int max_slots = 256;
   Server* server = nullptr;
+  double wait_s = 0.0;   // > 0: the longest a call waits for the device (HWENO_ERR_TIMEOUT)
 };
 
 static int fail(hweno_engine* e, int code, const std::string& m) {
@@ -398,6 +399,13 @@ const char* hweno_last_error(const hweno_engine* e) { return e ? e->err.c_str() 
 
 void* hweno_engine_stream(hweno_engine* e) { return e ? (void*)e->stream : nullptr; }
 
+int hweno_set_wait_limit(hweno_engine* e, double seconds) {
+  if (!e || !(seconds >= 0.0)) return fail(e, HWENO_ERR_ARG, "invalid wait limit");
+  std::lock_guard<std::recursive_mutex> lk(e->mu);
+  e->wait_s = seconds;
+  return HWENO_OK;
+}
+
 }  // extern "C"
 
 // ---- internal entry points shared with the server ------------------------------------
@@ -448,7 +456,8 @@ int engine_load_state(hweno_engine* e, Solve* s, const double* host, double t, c
   if (host) CUDA_TRY(e, cudaMemcpyAsync(s->U0, host, sizeof(double) * s->nU,
                                         cudaMemcpyHostToDevice, st));
   DevScal* h = s->host;
-  CUDA_TRY(e, cudaStreamSynchronize(st));
+  int rc = engine_wait(e, st, false);   // the copy reads the caller's buffer
+  if (rc) return rc;
   std::memset(h, 0, sizeof(DevScal));
   h->t = t;
   h->t_end = t;
@@ -458,15 +467,15 @@ int engine_load_state(hweno_engine* e, Solve* s, const double* host, double t, c
   h->step_limit = 0;
   CUDA_TRY(e, cudaMemcpyAsync(s->sc, h, sizeof(DevScal), cudaMemcpyHostToDevice, st));
   CUDA_TRY(e, launch_alpha(s->prob.equation, s->prob.dim, s->kp, s->U0, s->sc->alpha[3], st));
-  CUDA_TRY(e, cudaStreamSynchronize(st));
-  return HWENO_OK;
+  return engine_wait(e, st, false);
 }
 
 // set the run target on the device (t_end, absolute step limit)
 int engine_set_target(hweno_engine* e, Solve* s, double t_end, long long step_limit,
                       cudaStream_t st) {
   CUDA_TRY(e, cudaMemcpyAsync(s->host, s->sc, sizeof(DevScal), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(e, cudaStreamSynchronize(st));
+  int rc = engine_wait(e, st, true);
+  if (rc) return rc;
   s->host->t_end = t_end;
   s->host->step_limit = step_limit;
   CUDA_TRY(e, cudaMemcpyAsync(&s->sc->t_end, &s->host->t_end, sizeof(double),
@@ -488,7 +497,8 @@ int engine_conservation(hweno_engine* e, Solve* s, double* sums, double* abs_sum
   CUDA_TRY(e, cudaGetLastError());
   CUDA_TRY(e, cudaMemcpyAsync(s->cons_host, s->cons + 2 * s->nc * kConsBlocks,
                               sizeof(double) * 2 * s->nc, cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(e, cudaStreamSynchronize(st));
+  int rc = engine_wait(e, st, true);
+  if (rc) return rc;
   for (int c = 0; c < s->nc; ++c) {
     if (sums) sums[c] = s->cons_host[2 * c];
     if (abs_sums) abs_sums[c] = s->cons_host[2 * c + 1];
@@ -496,10 +506,30 @@ int engine_conservation(hweno_engine* e, Solve* s, double* sums, double* abs_sum
   return HWENO_OK;
 }
 
+// Wait for the work queued on st: without a limit (or when `bounded` is false: a copy to or
+// from a caller's host buffer is in flight, which must finish before the call returns),
+// cudaStreamSynchronize; with one, poll the stream (yielding the thread) until it is done or
+// the limit has passed, then return HWENO_ERR_TIMEOUT.  The queued work is not cancelled: it
+// completes on its own, and the next call that waits sees its results.
+int engine_wait(hweno_engine* e, cudaStream_t st, bool bounded) {
+  if (!bounded || !(e->wait_s > 0.0)) {
+    CUDA_TRY(e, cudaStreamSynchronize(st));
+    return HWENO_OK;
+  }
+  const double t0 = now_seconds();
+  for (;;) {
+    const cudaError_t q = cudaStreamQuery(st);
+    if (q == cudaSuccess) return HWENO_OK;
+    if (q != cudaErrorNotReady) return cuda_fail(e, q, "waiting for the device");
+    if (now_seconds() - t0 > e->wait_s)
+      return fail(e, HWENO_ERR_TIMEOUT, "the device work was not done within the wait limit");
+    std::this_thread::yield();
+  }
+}
+
 int engine_read_scalars(hweno_engine* e, Solve* s, cudaStream_t st) {
   CUDA_TRY(e, cudaMemcpyAsync(s->host, s->sc, sizeof(DevScal), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(e, cudaStreamSynchronize(st));
-  return HWENO_OK;
+  return engine_wait(e, st, true);
 }
 
 static int ensure_graph(hweno_engine* e, Solve* s, int steps) {
@@ -539,7 +569,7 @@ int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps,
     for (long long b = 0; b < batch; ++b) CUDA_TRY(e, cudaGraphLaunch(s->graph, e->stream));
     rc = engine_read_scalars(e, s, e->stream);
     if (rc) return rc;
-    if (s->host->status) break;
+    if (s->host->status & kStatusNonphysical) break;
     if (!(s->host->t < t_end) || s->host->steps >= limit) break;
     // size the next batch from the steps left at the current dt
     double left = (t_end - s->host->t) / std::max(s->host->dt, 1e-300);
@@ -547,7 +577,7 @@ int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps,
     batch = std::max<long long>(1, std::min<long long>(64, (want + G - 1) / G));
   }
   if (steps_taken) *steps_taken = s->host->steps - steps0;
-  if (s->host->status) return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
+  if (s->host->status & kStatusNonphysical) return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
   return HWENO_OK;
 }
 
@@ -635,7 +665,9 @@ int hweno_get_state(hweno_engine* e, uint64_t id, double* host, double* t) {
   if (host)
     CUDA_TRY(e, cudaMemcpyAsync(host, s->U0, sizeof(double) * s->nU, cudaMemcpyDeviceToHost,
                                 e->stream));
-  int rc = engine_read_scalars(e, s, e->stream);
+  CUDA_TRY(e, cudaMemcpyAsync(s->host, s->sc, sizeof(DevScal), cudaMemcpyDeviceToHost,
+                              e->stream));
+  int rc = engine_wait(e, e->stream, false);   // the copy writes the caller's buffer
   if (rc) return rc;
   if (t) *t = s->host->t;
   return HWENO_OK;
@@ -664,7 +696,7 @@ int hweno_step(hweno_engine* e, uint64_t id, double* dt_taken) {
   rc = engine_read_scalars(e, s, e->stream);
   if (rc) return rc;
   if (dt_taken) *dt_taken = s->host->dt;
-  if (s->host->status) return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
+  if (s->host->status & kStatusNonphysical) return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
   return HWENO_OK;
 }
 

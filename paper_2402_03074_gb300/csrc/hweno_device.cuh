@@ -35,6 +35,12 @@ __device__ __forceinline__ R kconst(double d, float f) {
   else return d;
 }
 
+// Bits of a stage's status word: a non-physical output (rho <= 0, p <= 0 or a non-finite
+// value; an error), and, for information only, a cell whose weights needed the direct formula
+// (2D; data scaled by about 2^+-50 or more).
+constexpr uint32_t kStatusNonphysical = 1u;
+constexpr uint32_t kStatusDirectWeights = 2u;
+
 // Pointers and scalars of one stage launch.
 struct KStage {
   const double* Uin;   // stage input (stencil reads)
@@ -86,27 +92,38 @@ __device__ __forceinline__ double mirror_sign(int c, int m, int fx, int fy) {
   return s;
 }
 
-// Reciprocal 1/x: the single-precision reciprocal of x refined by one third-order step of
-// Householder's iteration for 1/x, y <- y + y (e + e^2) with e = 1 - x y: the new residual is
-// 1 - x y (1 + e + e^2) = e^3, so the seed's < 2^-22 relative error drops below 2^-66, under
-// the final rounding (result within 1 ulp of 1/x).  The double <-> float format changes of the
-// seed are done on the integer bits (x's significand truncated to 23 bits; the float result
-// widened exactly), so only three FMAs use the FP64 pipe.  Values whose exponent is outside
-// +-100 of 1 (where the float seed could over- or underflow) use the division.
-__device__ __forceinline__ double rcp_nr(double x) {
+// Reciprocal 1/x of a normal double whose exponent field eb lies in [1, 2044] (so 1/x is
+// normal too), with no branch: x = m 2^(eb-1023) with m in [1, 2); the single-precision
+// reciprocal of m (m's significand truncated to 23 bits, the format changes done on the
+// integer bits) refined by one third-order step of Householder's iteration for 1/m,
+// y <- y + y (e + e^2) with e = 1 - m y (the new residual is e^3: the seed's < 2^-22 relative
+// error drops below 2^-66, under the final rounding, so 1/m is within 1 ulp); then
+// 1/x = (1/m) 2^(1023-eb), an exact change of the exponent field.  Three FMAs use the FP64
+// pipe.
+__device__ __forceinline__ double rcp_normal(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int eb = (int)((b >> 52) & 0x7ff);
-  if (eb < 1023 - 100 || eb > 1023 + 100) return 1.0 / x;
-  const unsigned int xf = (unsigned int)(b >> 32) & 0x80000000u |
-                          (unsigned int)(eb - 1023 + 127) << 23 |
+  const long long eb = (long long)((b >> 52) & 0x7ff);
+  const double m = __longlong_as_double((long long)((b & 0x800fffffffffffffull) |
+                                                    0x3ff0000000000000ull));
+  const unsigned int mf = (unsigned int)(b >> 32) & 0x80000000u | (127u << 23) |
                           (unsigned int)(b >> 29) & 0x7fffffu;
-  const unsigned int rf = __float_as_uint(__frcp_rn(__uint_as_float(xf)));
+  const unsigned int rf = __float_as_uint(__frcp_rn(__uint_as_float(mf)));  // in (0.5, 1]
   const unsigned long long yb = (unsigned long long)(rf & 0x80000000u) << 32 |
                                 (unsigned long long)((rf >> 23 & 0xffu) - 127u + 1023u) << 52 |
                                 (unsigned long long)(rf & 0x7fffffu) << 29;
   const double y = __longlong_as_double((long long)yb);
-  const double e = fma(-x, y, 1.0);
-  return fma(y, fma(e, e, e), y);
+  const double e = fma(-m, y, 1.0);
+  const double r = fma(y, fma(e, e, e), y);  // 1/m, exponent field 1022 or 1023
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(r) +
+                                          ((unsigned long long)(1023ll - eb) << 52)));
+}
+
+// 1/x for any x: rcp_normal where it applies; zeros, subnormals, infinities, NaNs and the
+// few largest exponents take the division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const int eb = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+  if (eb < 1 || eb > 2044) return 1.0 / x;
+  return rcp_normal(x);
 }
 
 // Format changes between float and double on the integer bits, for the FP32-bulk path, where
@@ -171,17 +188,16 @@ __device__ __forceinline__ double rcp<double>(double x) { return rcp_nr(x); }
 // D_m = prod_{k != m} d_k, omega_m = gamma_m (D + tau D_m) / S, S = sum_k gamma_k (D + tau D_k)
 // (equal to the direct formula in exact arithmetic), so a0 = (D + tau D_0) / S and
 // b_m = gamma_m tau (D_m - D_0) / S: one reciprocal, and no cancellation beyond that of
-// D_m - D_0.  If the products leave the normal double range the direct formula is used.
+// D_m - D_0.  The product form needs D and S normal and far from overflow; where they are not
+// (data scaled by about 2^+-100 or more), the direct formula is used instead.
+//
+// nonlinear_weights_fast evaluates the product form without a branch and returns whether it
+// applies (the caller then runs nonlinear_weights_direct for the cells where it does not), so
+// that the weight chains of several fields can share one basic block.
 template <int NS>
-__device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], double uave,
-                                                  const KProblem& P, double& a0,
-                                                  double (&b)[NS]) {
-  if (P.wmode == 2) {   // linear weights (omega = gamma): the combined polynomial is p_0
-    a0 = 1.0;
-#pragma unroll
-    for (int m = 0; m < NS; ++m) b[m] = 0.0;
-    return;
-  }
+__device__ __forceinline__ bool nonlinear_weights_fast(const double (&beta)[NS], double uave,
+                                                       const KProblem& P, double& a0,
+                                                       double (&b)[NS]) {
   double s = fabs(beta[0] - beta[1]);
 #pragma unroll
   for (int m = 2; m < NS; ++m) s += fabs(beta[0] - beta[m]);
@@ -212,30 +228,57 @@ __device__ __forceinline__ void nonlinear_weights(const double (&beta)[NS], doub
   for (int m = 2; m < NS; ++m) dsum += Dm[m];
   const double nsum = fma(tau, dsum, (double)(NS - 1) * D);
   const double S = fma(g0, N0, P.glo * nsum);
-  // exponent checks on the INT pipe: D and S must be normal and far from overflow
+  // exponent checks on the INT pipe: D and S must be normal and far from overflow (which also
+  // keeps S inside the range of rcp_normal)
   const long long eD = (__double_as_longlong(D) >> 52) & 0x7ff;
   const long long eS = (__double_as_longlong(S) >> 52) & 0x7ff;
-  if (eD > 64 && eD < 2047 - 64 && eS > 64 && eS < 2047 - 64) {
-    const double inv = rcp_nr(S);
-    a0 = N0 * inv;
-    const double k = (tau * P.glo) * inv;
+  const bool ok = eD > 64 && eD < 2047 - 64 && eS > 64 && eS < 2047 - 64;
+  const double inv = rcp_normal(S);
+  const double k = (tau * P.glo) * inv;
+  const bool lin = P.wmode == 2;   // linear weights (omega = gamma): the polynomial is p_0
+  a0 = lin ? 1.0 : N0 * inv;
 #pragma unroll
-    for (int m = 1; m < NS; ++m) b[m] = k * (Dm[m] - Dm[0]);
-  } else {
-    double wt[NS];
-    double ws = 0.0;
-#pragma unroll
-    for (int m = 0; m < NS; ++m) {
-      const double gm = (m == 0) ? g0 : P.glo;
-      wt[m] = fma(gm, tau / d[m], gm);
-      ws += wt[m];
-    }
-    const double inv = 1.0 / ws;
-    a0 = (wt[0] * inv) / g0;
-#pragma unroll
-    for (int m = 1; m < NS; ++m) b[m] = wt[m] * inv - a0 * P.glo;
-  }
+  for (int m = 1; m < NS; ++m) b[m] = lin ? 0.0 : k * (Dm[m] - Dm[0]);
   b[0] = 0.0;
+  return ok || lin;
+}
+
+// The direct formula of Eq. 2.11 / 2.22 (divisions), for the data where the product form
+// would leave the normal range.
+template <int NS>
+__device__ __noinline__ void nonlinear_weights_direct(const double (&beta)[NS], double uave,
+                                                      const KProblem& P, double& a0,
+                                                      double (&b)[NS]) {
+  double s = fabs(beta[0] - beta[1]);
+#pragma unroll
+  for (int m = 2; m < NS; ++m) s += fabs(beta[0] - beta[m]);
+  s *= 1.0 / (double)(NS - 1);
+  const double tau = s * s;
+  const double ua = (P.wmode == 1) ? 1.0 : uave;
+  const double g0 = P.g0[NS == 3 ? 0 : 1];
+  double wt[NS];
+  double ws = 0.0;
+#pragma unroll
+  for (int m = 0; m < NS; ++m) {
+    const double gm = (m == 0) ? g0 : P.glo;
+    wt[m] = fma(gm, tau / fma(beta[m], ua, P.eps), gm);
+    ws += wt[m];
+  }
+  const double inv = 1.0 / ws;
+  a0 = (wt[0] * inv) / g0;
+#pragma unroll
+  for (int m = 1; m < NS; ++m) b[m] = wt[m] * inv - a0 * P.glo;
+  b[0] = 0.0;
+}
+
+// Returns false where the direct formula was needed.
+template <int NS>
+__device__ __forceinline__ bool nonlinear_weights(const double (&beta)[NS], double uave,
+                                                  const KProblem& P, double& a0,
+                                                  double (&b)[NS]) {
+  if (nonlinear_weights_fast<NS>(beta, uave, P, a0, b)) return true;
+  nonlinear_weights_direct<NS>(beta, uave, P, a0, b);
+  return false;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -299,16 +342,17 @@ __device__ __forceinline__ void recon1d(R um, R u0, R up, R vm, R vp, const KPro
 // 2D reconstruction of one field (Sec. 2.2 Steps 1-3, Eq. 2.23).
 // u[0..8]: averages of cells 1..9 (row-major from the bottom-left, u[4] = own cell);
 // v[0..3], w[0..3]: x / y first moments of cells 2, 4, 6, 8.
-// Output: combined monomial coefficients C[15] (basis 1, xi, eta, xi^2, xi eta, eta^2,
-// xi^3, xi^2 eta, xi eta^2, eta^3, xi^4, xi^3 eta, xi^2 eta^2, xi eta^3, eta^4).
+
+// Step 1: the Appendix coefficients of p_0 (c_{0,4} with -7/22 u_1), written on symmetric
+// combinations of the stencil; basis 1, xi, eta, xi^2, xi eta, eta^2, xi^3, xi^2 eta,
+// xi eta^2, eta^3, xi^4, xi^3 eta, xi^2 eta^2, xi eta^3, eta^4.
 template <typename R>
-__device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
-                                               const KProblem& P, R (&C)[15]) {
+__device__ __forceinline__ void coeffs2d(const R (&u)[9], const R (&v)[4], const R (&w)[4],
+                                         R (&c)[15]) {
   const R u1 = u[0], u2 = u[1], u3 = u[2], u4 = u[3], u5 = u[4], u6 = u[5], u7 = u[6],
           u8 = u[7], u9 = u[8];
   const R v2 = v[0], v4 = v[1], v6 = v[2], v8 = v[3];
   const R w2 = w[0], w4 = w[1], w6 = w[2], w8 = w[3];
-  // Step 1: Appendix (c_{0,4} with -7/22 u_1), written on symmetric combinations
   const R A = u1 + u3, B = u7 + u9, Sc = A + B;
   const R Db = u1 - u3, Dt = u7 - u9;
   const R X1 = Db + Dt, X2 = A - B, X3 = Db - Dt;
@@ -316,7 +360,6 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
   const R Se = h + vv;
   const R Va = v4 + v6, Vd = v6 - v4, Wa = w2 + w8, Wd = w8 - w2;
   const R v82 = v8 - v2, w64 = w6 - w4;
-  R c[15];
   c[0] = R(1.0 / 576.0) * Sc - R(133.0 / 1152.0) * Se + R(419.0 / 288.0) * u5 +
          R(27.0 / 64.0) * (Vd + Wd);
   c[1] = R(1.0 / 48.0) * X1 - R(397.0 / 456.0) * e - R(75.0 / 19.0) * Va;
@@ -335,73 +378,105 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
   c[12] = R(0.25) * Sc - R(0.5) * Se + u5;
   c[13] = R(5.0 / 22.0) * X3 - R(60.0 / 11.0) * w64;
   c[14] = R(-5.0 / 8.0) * vv + R(5.0 / 4.0) * u5 + R(15.0 / 4.0) * Wd;
-  // linear polynomials on S_1 = {2,4,5}, S_2 = {2,5,6}, S_3 = {4,5,8}, S_4 = {5,6,8}
-  const R dl = u5 - u4, dr = u6 - u5, db = u5 - u2, dtp = u8 - u5;
-  // Step 2: Eq. 2.20 (double)
-  double beta[5];
-  {
-    double d[15];
+}
+
+// Steps 2-3 inputs: the smoothness indicators of Eq. 2.20 (double) of p_0 (coefficients c)
+// and of the linear polynomials on S_1 = {2,4,5}, S_2 = {2,5,6}, S_3 = {4,5,8}, S_4 = {5,6,8}
+// (slopes u5 - u4, u6 - u5, u5 - u2, u8 - u5), and u_ave of Eq. 2.22.
+template <typename R>
+__device__ __forceinline__ void beta2d(const R (&c)[15], const R (&u)[9], double (&beta)[5],
+                                       double& uave) {
+  double d[15];
 #pragma unroll
-    for (int n = 0; n < 15; ++n) d[n] = to_f64(c[n]);
-    double s, t;
-    t = fma(0.5, d[6], d[1]);
-    s = t * t;
-    t = fma(1.0 / 6.0, d[8], d[1]);
-    s = fma(t, t, s);
-    t = fma(1.0 / 6.0, d[7], d[2]);
-    s = fma(t, t, s);
-    t = fma(0.5, d[9], d[2]);
-    s = fma(t, t, s);
-    double b = 0.5 * s;
-    t = fma(63.0 / 65.0, d[10], d[3]);
-    s = t * t;
-    t = fma(1.0 / 6.0, d[12], d[3]);
-    s = fma(t, t, s);
-    t = fma(1.0 / 6.0, d[12], d[5]);
-    s = fma(t, t, s);
-    t = fma(63.0 / 65.0, d[14], d[5]);
-    s = fma(t, t, s);
-    b = fma(13.0 / 6.0, s, b);
-    t = fma(17.0 / 35.0, d[11], d[4]);
-    s = t * t;
-    t = fma(17.0 / 35.0, d[13], d[4]);
-    s = fma(t, t, s);
-    b = fma(7.0 / 12.0, s, b);
-    t = fma(5.0 / 9357.0, d[8], d[6]);
-    b = fma(3119.0 / 80.0 * t, t, b);
-    t = fma(15.0 / 3379.0, d[9], d[7]);
-    b = fma(3379.0 / 720.0 * t, t, b);
-    b = fma(2634769.0 / 561420.0 * d[8], d[8], b);
-    b = fma(2634769.0 / 67580.0 * d[9], d[9], b);
-    t = fma(3185.0 / 11353166.0, d[12], d[10]);
-    b = fma(5676583.0 / 9100.0 * t, t, b);
-    t = fma(1155.0 / 709573.0, d[13], d[11]);
-    b = fma(709573.0 / 16800.0 * t, t, b);
-    t = fma(2145748374.0 / 230094013357.0, d[14], d[12]);
-    b = fma(230094013357.0 / 12261419280.0 * t, t, b);
-    b = fma(31468281769.0 / 745051650.0 * d[13], d[13], b);
-    b = fma(25118160529227568.0 / 40266452337475.0 * d[14], d[14], b);
-    beta[0] = b;
-    const double el = to_f64(dl), er = to_f64(dr), eb = to_f64(db), et = to_f64(dtp);
-    const double el2 = el * el, er2 = er * er, eb2 = eb * eb, et2 = et * et;
-    beta[1] = el2 + eb2;
-    beta[2] = er2 + eb2;
-    beta[3] = el2 + et2;
-    beta[4] = er2 + et2;
-  }
-  // Step 3
-  const double a = (to_f64(fabs(u2)) + to_f64(fabs(u4)) + to_f64(fabs(u5)) + to_f64(fabs(u6)) +
-                    to_f64(fabs(u8))) * 0.2;
-  double a0d, bm[5];
-  nonlinear_weights<5>(beta, a * a, P, a0d, bm);
-  const R a0 = from_f64<R>(a0d);
-  const R b1 = from_f64<R>(bm[1]), b2 = from_f64<R>(bm[2]), b3 = from_f64<R>(bm[3]),
-          b4 = from_f64<R>(bm[4]);
-  C[0] = a0 * c[0] + from_f64<R>(1.0 - a0d) * u5;
+  for (int n = 0; n < 15; ++n) d[n] = to_f64(c[n]);
+  double s, t;
+  t = fma(0.5, d[6], d[1]);
+  s = t * t;
+  t = fma(1.0 / 6.0, d[8], d[1]);
+  s = fma(t, t, s);
+  t = fma(1.0 / 6.0, d[7], d[2]);
+  s = fma(t, t, s);
+  t = fma(0.5, d[9], d[2]);
+  s = fma(t, t, s);
+  double b = 0.5 * s;
+  t = fma(63.0 / 65.0, d[10], d[3]);
+  s = t * t;
+  t = fma(1.0 / 6.0, d[12], d[3]);
+  s = fma(t, t, s);
+  t = fma(1.0 / 6.0, d[12], d[5]);
+  s = fma(t, t, s);
+  t = fma(63.0 / 65.0, d[14], d[5]);
+  s = fma(t, t, s);
+  b = fma(13.0 / 6.0, s, b);
+  t = fma(17.0 / 35.0, d[11], d[4]);
+  s = t * t;
+  t = fma(17.0 / 35.0, d[13], d[4]);
+  s = fma(t, t, s);
+  b = fma(7.0 / 12.0, s, b);
+  t = fma(5.0 / 9357.0, d[8], d[6]);
+  b = fma(3119.0 / 80.0 * t, t, b);
+  t = fma(15.0 / 3379.0, d[9], d[7]);
+  b = fma(3379.0 / 720.0 * t, t, b);
+  b = fma(2634769.0 / 561420.0 * d[8], d[8], b);
+  b = fma(2634769.0 / 67580.0 * d[9], d[9], b);
+  t = fma(3185.0 / 11353166.0, d[12], d[10]);
+  b = fma(5676583.0 / 9100.0 * t, t, b);
+  t = fma(1155.0 / 709573.0, d[13], d[11]);
+  b = fma(709573.0 / 16800.0 * t, t, b);
+  t = fma(2145748374.0 / 230094013357.0, d[14], d[12]);
+  b = fma(230094013357.0 / 12261419280.0 * t, t, b);
+  b = fma(31468281769.0 / 745051650.0 * d[13], d[13], b);
+  b = fma(25118160529227568.0 / 40266452337475.0 * d[14], d[14], b);
+  beta[0] = b;
+  const double el = to_f64(u[4] - u[3]), er = to_f64(u[5] - u[4]), eb = to_f64(u[4] - u[1]),
+               et = to_f64(u[7] - u[4]);
+  const double el2 = el * el, er2 = er * er, eb2 = eb * eb, et2 = et * et;
+  beta[1] = el2 + eb2;
+  beta[2] = er2 + eb2;
+  beta[3] = el2 + et2;
+  beta[4] = er2 + et2;
+  const double a = (to_f64(fabs(u[1])) + to_f64(fabs(u[3])) + to_f64(fabs(u[4])) +
+                    to_f64(fabs(u[5])) + to_f64(fabs(u[7]))) * 0.2;
+  uave = a * a;
+}
+
+// The combined polynomial (Eq. 2.23) a0 p_0 + sum_m b_m p_m in monomial coefficients C;
+// om = 1 - a0 (formed in double by the caller: the constant term of the p_m is u5).
+template <typename R>
+__device__ __forceinline__ void combine2d(const R (&c)[15], const R (&u)[9], R a0, R om,
+                                          R b1, R b2, R b3, R b4, R (&C)[15]) {
+  const R dl = u[4] - u[3], dr = u[5] - u[4], db = u[4] - u[1], dtp = u[7] - u[4];
+  C[0] = a0 * c[0] + om * u[4];
   C[1] = a0 * c[1] + (b1 + b3) * dl + (b2 + b4) * dr;
   C[2] = a0 * c[2] + (b1 + b2) * db + (b3 + b4) * dtp;
 #pragma unroll
   for (int n = 3; n < 15; ++n) C[n] = a0 * c[n];
+}
+
+// One field, Steps 1-3: combined monomial coefficients C[15].
+// WMODE 0: the weights by nonlinear_weights (product form, direct formula where it does not
+// apply; `ok` cleared where the direct formula was used); 1: the product form alone, without
+// a branch, `ok` cleared where it does not apply (the caller redoes those cells with WMODE 2);
+// 2: the direct formula.
+template <typename R, int WMODE = 0>
+__device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
+                                               const KProblem& P, R (&C)[15], bool& ok) {
+  R c[15];
+  coeffs2d<R>(u, v, w, c);
+  double beta[5], uave;
+  beta2d<R>(c, u, beta, uave);
+  double a0d, bm[5];
+  if constexpr (WMODE == 0) ok &= nonlinear_weights<5>(beta, uave, P, a0d, bm);
+  else if constexpr (WMODE == 1) ok &= nonlinear_weights_fast<5>(beta, uave, P, a0d, bm);
+  else nonlinear_weights_direct<5>(beta, uave, P, a0d, bm);
+  combine2d<R>(c, u, from_f64<R>(a0d), from_f64<R>(1.0 - a0d), from_f64<R>(bm[1]),
+               from_f64<R>(bm[2]), from_f64<R>(bm[3]), from_f64<R>(bm[4]), C);
+}
+template <typename R>
+__device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
+                                               const KProblem& P, R (&C)[15]) {
+  bool ok = true;
+  recon2d_coeffs<R, 0>(u, v, w, P, C, ok);
 }
 
 // Gauss node sqrt(15)/10 and powers

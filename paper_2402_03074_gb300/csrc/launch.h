@@ -62,13 +62,20 @@ __device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_
 struct TileShape {
   int rows = 0;
   int bands = 0;
+  // 1D: block width (0 = the default rule, else 32, 64 or 128 threads) and threads per cell
+  // (0 or 1: one thread per cell; 4: one lane per characteristic field, 1D Euler with the
+  // characteristic decomposition)
+  int width = 0;
+  int lanes = 0;
 };
-// Tuning table keyed by (equation, characteristic, precision, nx, ny); {0, 0} = not tuned.
+// Tuning table keyed by (equation, characteristic, precision, nx, ny); all zero = not tuned.
 TileShape tuning_shape(int eq, int characteristic, int mixed, int nx, int ny);
 void tuning_set_shape(int eq, int characteristic, int mixed, int nx, int ny, TileShape t);
 // Shape override for the next 2D launches of this thread (autotuner): rows / bands > 0 fix
 // them, -1 the default geometry ignoring the table, {0, 0} no override.
 void tuning_force_shape(TileShape t);
+// The same for 1D launches (block width and threads per cell); all zero = no override.
+void tuning_force_shape1d(TileShape t);
 
 // One stage of the modified SSP-RK3 over a whole grid (1D / 2D), asynchronous on st.
 cudaError_t launch_stage1d(int eq, bool characteristic, bool mixed, const KProblem& P,

@@ -355,14 +355,18 @@ static int serve_once(Server* S, long long max_steps) {
   gather_scalars_kernel<<<(n + 127) / 128, 128, 0, st>>>(S->d_dt, S->d_gather);
   SRV_TRY(cudaGetLastError());
   SRV_TRY(cudaMemcpyAsync(S->h_gather, S->d_gather, sizeof(DevScal) * n, cudaMemcpyDeviceToHost, st));
-  SRV_TRY(cudaStreamSynchronize(st));
+  {
+    // the served iteration's one wait for the device (bounded by hweno_set_wait_limit)
+    const int rc = engine_wait(e, st, true);
+    if (rc) return rc;
+  }
   std::vector<Request*> still;
   for (size_t q = 0; q < S->live.size(); ++q) {
     Request* r = S->live[q];
     const DevScal& d = S->h_gather[q];
     r->t = d.t;
     r->steps = d.steps;
-    if (d.status) {
+    if (d.status & kStatusNonphysical) {
       finish(S, r, HWENO_ERR_NONPHYSICAL);
       S->dirty = true;
     } else if (!(d.t < r->prob.t_end)) {
@@ -462,7 +466,7 @@ int hweno_serve(hweno_engine* e, int64_t max_steps, int* active) {
   cudaSetDevice(engine_device(e));
   int rc = serve_once(s, max_steps < 1 ? 1 : max_steps);
   if (active) *active = (int)(s->live.size() + s->queue.size());
-  if (rc) engine_set_error(e, "serving iteration failed: " + g_srv_err);
+  if (rc && rc != HWENO_ERR_TIMEOUT) engine_set_error(e, "serving iteration failed: " + g_srv_err);
   return rc;
 }
 

@@ -24,6 +24,7 @@ int engine_load_state(hweno_engine* e, Solve* s, const double* host, double t, c
 int engine_set_target(hweno_engine* e, Solve* s, double t_end, long long step_limit,
                       cudaStream_t st);
 int engine_read_scalars(hweno_engine* e, Solve* s, cudaStream_t st);
+int engine_wait(hweno_engine* e, cudaStream_t st, bool bounded);
 int engine_conservation(hweno_engine* e, Solve* s, double* sums, double* abs_sums,
                         cudaStream_t st);
 int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps, long long* steps);

@@ -11,6 +11,10 @@
 
 namespace hw {
 
+// 1D shape override of the autotuner (this thread's next launches); zero = none
+static thread_local TileShape g_force1d;
+void tuning_force_shape1d(TileShape t) { g_force1d = t; }
+
 static int sm_count() {
   static int cache[64] = {};
   int dev = 0;
@@ -29,10 +33,34 @@ __global__ void __launch_bounds__(BW) stage1d_kernel(KProblem P, KStage S) {
   stage1d_item<EQ, CHAR, R, BW>(P, S, blockIdx.x);
 }
 
+template <typename R, int BW>
+__global__ void __launch_bounds__(BW) stage1d_fields_kernel(KProblem P, KStage S) {
+  if (S.active && *S.active == 0) return;
+  stage1d_fields_item<R, BW>(P, S, blockIdx.x);
+}
+
+// blocks of BW threads, BW - 2 cells each (one thread per cell), or BW / 4 - 2 cells each
+// (one lane per characteristic field)
 template <int EQ, bool CHAR, typename R>
 static cudaError_t launch1d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
+  TileShape ts;
+  if (g_force1d.width || g_force1d.lanes) ts = g_force1d;
+  else ts = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, 1);
+  if constexpr (EQ == EQ_EULER && CHAR) {
+    if (ts.lanes == 4) {
+      const int w = ts.width ? ts.width : 128;
+      if (w == 32)
+        stage1d_fields_kernel<R, 32><<<(P.nx + 5) / 6, 32, 0, st>>>(P, S);
+      else if (w == 64)
+        stage1d_fields_kernel<R, 64><<<(P.nx + 13) / 14, 64, 0, st>>>(P, S);
+      else
+        stage1d_fields_kernel<R, 128><<<(P.nx + 29) / 30, 128, 0, st>>>(P, S);
+      return cudaGetLastError();
+    }
+  }
   const int wide = (P.nx + 125) / 126;
-  if (wide >= sm_count()) {
+  const int w = ts.width ? ts.width : (wide >= sm_count() ? 128 : 32);
+  if (w == 128) {
     stage1d_kernel<EQ, CHAR, R, 128><<<wide, 128, 0, st>>>(P, S);
   } else {
     stage1d_kernel<EQ, CHAR, R, 32><<<(P.nx + 29) / 30, 32, 0, st>>>(P, S);
@@ -45,7 +73,16 @@ static size_t local1d_t() {
   cudaFuncAttributes fa, fb;
   if (cudaFuncGetAttributes(&fa, stage1d_kernel<EQ, CHAR, R, 128>) != cudaSuccess) return 0;
   if (cudaFuncGetAttributes(&fb, stage1d_kernel<EQ, CHAR, R, 32>) != cudaSuccess) return 0;
-  return fa.localSizeBytes > fb.localSizeBytes ? fa.localSizeBytes : fb.localSizeBytes;
+  size_t m = fa.localSizeBytes > fb.localSizeBytes ? fa.localSizeBytes : fb.localSizeBytes;
+  if constexpr (EQ == EQ_EULER && CHAR) {
+    cudaFuncAttributes f1, f2, f3;
+    if (cudaFuncGetAttributes(&f1, stage1d_fields_kernel<R, 32>) != cudaSuccess ||
+        cudaFuncGetAttributes(&f2, stage1d_fields_kernel<R, 64>) != cudaSuccess ||
+        cudaFuncGetAttributes(&f3, stage1d_fields_kernel<R, 128>) != cudaSuccess)
+      return 0;
+    for (size_t x : {f1.localSizeBytes, f2.localSizeBytes, f3.localSizeBytes}) m = x > m ? x : m;
+  }
+  return m;
 }
 
 cudaError_t prepare_stage1d(size_t* max_local) {

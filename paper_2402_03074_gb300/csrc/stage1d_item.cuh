@@ -158,11 +158,147 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
       wmax = Phys<EQ, double>::speed(P, 0, ua);
     }
     if (bad) {
-      atomicOr(S.status, 1u);
+      atomicOr(S.status, kStatusNonphysical);
       wmax = 0.0;
     }
   }
   // block max -> one atomic per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  if ((t & 31) == 0) red[t >> 5] = wmax;
+  __syncthreads();
+  if (t == 0) {
+    double m = red[0];
+#pragma unroll
+    for (int w = 1; w < BW / 32; ++w) m = fmax(m, red[w]);
+    atomic_max_nonneg(&S.alpha_out[0], m);
+  }
+  __syncthreads();  // the block may start another item in the same shared memory
+}
+
+// One lane per characteristic field (1D Euler with the characteristic decomposition): the
+// lanes 4q .. 4q+3 of the block stand for cell slot q, cell i = i0 - 1 + q with
+// i0 = blk (G - 2), G = BW / 4; lane 4q + f projects the stencil onto field f and runs its
+// reconstruction (Steps 1-3, Eq. 2.12; the fourth lane repeats field 2, unused), the four
+// lanes exchange the fields' point values and v-hat by warp shuffles, each unprojects them
+// and forms the fluxes, and lane 4q + c updates component c (Eq. 2.3, 2.13).  A cell's
+// serial FP64 work -- three field reconstructions one after the other in stage1d_item --
+// is split over three lanes, which shortens the dependent chain of a warp for grids too
+// short to fill the GPU with one thread per cell.  Every lane of a warp runs every shuffle.
+template <typename R, int BW>
+__device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KStage& S, int blk) {
+  constexpr int NC = 3, NM = 2, G = BW / 4;
+  const int nx = P.nx;
+  const int t = threadIdx.x, q = t >> 2, f = t & 3;
+  const int i0 = blk * (G - 2);
+  const int i = i0 - 1 + q;   // reconstructed cell of this lane's slot
+  const int lane0 = (t & 31) & ~3;
+
+  __shared__ R win[NC * NM][G + 2];   // moments of cells i0-2 .. i0+G-1 (bulk precision)
+  __shared__ R trL[NC][2][G];         // left trace (u, f) of each slot's cell
+  __shared__ R fhat[NC][G + 1];       // flux at the left face of slot q's cell
+  __shared__ double red[BW / 32];
+
+  for (int idx = t; idx < NC * NM * (G + 2); idx += BW) {
+    const int a = idx / (G + 2), col = idx % (G + 2);
+    const int c = a / NM, m = a % NM;
+    int flip;
+    const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
+    double val = S.Uin[(size_t)a * nx + ii];
+    if (flip) val *= mirror_sign<EQ_EULER, 1>(c, m, 1, 0);
+    win[a][col] = from_f64<R>(val);
+  }
+  __syncthreads();
+
+  const bool need = (i <= nx);
+  const bool upd = (q >= 1 && q <= G - 2 && i < nx);
+  // every lane computes (slots past the right ring read clamped columns; their results are
+  // not stored), so that the whole warp takes part in the shuffles
+  Eig1<R> E;
+  E.init(P, win[0][q + 1], win[2][q + 1], win[4][q + 1]);
+  const int fl = f < 3 ? f : 2;
+  auto proj = [&](int col, int m) -> R {   // field fl of moment m of window column col
+    const R U0 = win[0 + m][col], U1 = win[2 + m][col], U2 = win[4 + m][col];
+    const R s = E.b2h * U0 - E.b1h * (E.u * U1 - U2);
+    const R tt = (E.u * U0 - U1) * E.hic;
+    return fl == 0 ? s + tt : (fl == 1 ? U0 - R(2) * s : s - tt);
+  };
+  R p4[4], v;
+  recon1d<R>(proj(q, 0), proj(q + 1, 0), proj(q + 2, 0), proj(q, 1), proj(q + 2, 1), P, p4, v);
+  R cp[4][3], cv[3];
+#pragma unroll
+  for (int ff = 0; ff < 3; ++ff) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) cp[g][ff] = __shfl_sync(0xffffffffu, p4[g], lane0 + ff);
+    cv[ff] = __shfl_sync(0xffffffffu, v, lane0 + ff);
+  }
+  R pts[4][NC], vh[NC], fp[4][NC];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) E.unproject(cp[g], pts[g]);
+  E.unproject(cv, vh);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) euler_flux<1, R>(P, 0, pts[g], fp[g]);
+  if (need && f < NC) {
+    trL[f][0][q] = pts[0][f];
+    trL[f][1][q] = fp[0][f];
+  }
+  __syncthreads();
+  // LF flux at the right face of the slot's cell, component f (Eq. 2.4), once per face
+  const R alpha = (R)S.alpha_in[0];
+  if (need && f < NC && q < G - 1 && i < nx) {
+    const R uL = pts[3][f], fL = fp[3][f];
+    const R uR = trL[f][0][q + 1], fR = trL[f][1][q + 1];
+    fhat[f][q + 1] = R(0.5) * (fL + fR - alpha * (uR - uL));
+  }
+  __syncthreads();
+  // component f of the update (Eq. 2.3, 2.13)
+  double ou = 0.0, ov = 0.0;
+  bool bad = false;
+  if (upd && f < NC) {
+    const double dt = *S.dt;
+    const R idx = kconst<R>(P.inv_dx, P.inv_dxf);
+    const R fL = fhat[f][q], fR = fhat[f][q + 1];
+    const R F1 = -(fR - fL) * idx;
+    const R vol = R(1.0 / 12.0) * (fp[0][f] + fp[3][f]) + R(5.0 / 12.0) * (fp[1][f] + fp[2][f]);
+    const R F2 = (vol - R(0.5) * (fL + fR)) * idx;
+    const double own_u = (sizeof(R) == sizeof(double)) ? to_f64(win[f * NM][q + 1])
+                                                        : S.Uin[(size_t)(f * NM) * nx + i];
+    const double own_v = to_f64(vh[f]);
+    const size_t q0 = (size_t)(f * NM) * nx + i, q1 = q0 + nx;
+    double base_u, base_v;
+    if (S.k == 1) {
+      base_u = own_u;
+      base_v = own_v;
+      S.Vh[(size_t)f * nx + i] = own_v;
+    } else {
+      base_u = S.Un[q0];
+      base_v = S.Vh[(size_t)f * nx + i];
+    }
+    const double au = fma(dt, to_f64(F1), own_u), av = fma(dt, to_f64(F2), own_v);
+    if (S.k == 1) { ou = au; ov = av; }
+    else if (S.k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
+    else { ou = fma(1.0 / 3.0, base_u, 2.0 / 3.0 * au); ov = fma(1.0 / 3.0, base_v, 2.0 / 3.0 * av); }
+    S.Uout[q0] = ou;
+    S.Uout[q1] = ov;
+    bad = !finite_bits(ou) || !finite_bits(ov);
+  }
+  // wave speed and physicality of the output average: the slot's three components
+  double ua[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) ua[c] = __shfl_sync(0xffffffffu, ou, lane0 + c);
+  double wmax = 0.0;
+  if (upd && f == 0) {
+    double s0, s1;
+    const bool ok = euler_speeds<1>(P, ua, s0, s1);
+    if (ok) wmax = s0;
+    bad |= !ok;
+  }
+  bad = __shfl_sync(0xffffffffu, (int)bad, lane0) | __shfl_sync(0xffffffffu, (int)bad, lane0 + 1) |
+        __shfl_sync(0xffffffffu, (int)bad, lane0 + 2);
+  if (upd && f == 0 && bad) {
+    atomicOr(S.status, kStatusNonphysical);
+    wmax = 0.0;
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
   if ((t & 31) == 0) red[t >> 5] = wmax;

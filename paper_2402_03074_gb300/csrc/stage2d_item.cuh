@@ -115,6 +115,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   R pend[NC][3];                   // F^1..F^3 of (i, j-1) without its top face
   R pvh[NC], pwh[NC];              // v-hat, w-hat of (i, j-1)
   double wmax0 = 0.0, wmax1 = 0.0;
+  bool fast_weights = true;        // cleared where the direct-formula weights were needed
 
 #pragma unroll 1
   for (int j = j0 - 1; j <= j1; ++j) {
@@ -214,9 +215,8 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
             E.project_all(Vk, Wv_[e]);
             E.project_all(Zk, Ww[e]);
           }
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            R u[9], v[4], w[4];
+          // one field's stencil in characteristic variables
+          auto field = [&](int f, R (&u)[9], R (&v)[4], R (&w)[4]) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) u[k] = Wu[k][f];
 #pragma unroll
@@ -224,8 +224,9 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
               v[e] = Wv_[e][f];
               w[e] = Ww[e][f];
             }
-            R C[15];
-            recon2d_coeffs<R>(u, v, w, P, C);
+          };
+          // the combined polynomial of field f -> its points and modification
+          auto evaluate = [&](int f, const R (&C)[15]) {
             R ea[3], eb[3], in[9];
             if (pass == 0) {
               eval_xpass(C, ea, eb, in);
@@ -241,6 +242,16 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
             }
 #pragma unroll
             for (int p = 0; p < 9; ++p) ch[6 + p][f] = in[p];
+          };
+          // field by field: coefficients, FP64 smoothness indicators and weights (the
+          // branch-free product form, the direct formula only where it does not apply),
+          // combination and evaluation
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            R u[9], v[4], w[4], C[15];
+            field(f, u, v, w);
+            recon2d_coeffs<R, 0>(u, v, w, P, C, fast_weights);
+            evaluate(f, C);
           }
           R cons[16][4];
 #pragma unroll
@@ -291,7 +302,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
             w[e] = Wv(c * NM + 2, 2 * e + 1);
           }
           R C[15];
-          recon2d_coeffs<R>(u, v, w, P, C);
+          recon2d_coeffs<R, 0>(u, v, w, P, C, fast_weights);
           R ea[3], eb[3], in[9];
           eval_xpass(C, ea, eb, in);
 #pragma unroll
@@ -392,7 +403,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           wmax0 = fmax(wmax0, Phys<EQ, double>::speed(P, 0, ua));
           wmax1 = fmax(wmax1, Phys<EQ, double>::speed(P, 1, ua));
         }
-        if (bad) atomicOr(S.status, 1u);
+        if (bad) atomicOr(S.status, kStatusNonphysical);
       }
     }
 
@@ -442,8 +453,10 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
     red[0][t >> 5] = wmax0;
     red[1][t >> 5] = wmax1;
   }
-  __syncthreads();
+  const int any_direct = __syncthreads_or(fast_weights ? 0 : 1);
   if (t == 0) {
+    // informational status bit: some cell of the block needed the direct-formula weights
+    if (any_direct) atomicOr(S.status, kStatusDirectWeights);
     double m0 = red[0][0], m1 = red[1][0];
 #pragma unroll
     for (int w = 1; w < BW / 32; ++w) {

@@ -39,6 +39,10 @@ struct StaticScratch {
   StaticItem item[HWENO_STATIC_BATCH_MAX];
 };
 
+// It is passed by value to static_setup_kernel: keep it within the 4 KB kernel-parameter
+// limit that holds on every CUDA version.
+static_assert(sizeof(StaticScratch) <= 4096, "StaticScratch must fit a kernel parameter");
+
 // The scratch of hweno_stage_batch_static.  Every GPU that loads the library holds it (a few
 // KB) until the process exits; every call overwrites it, so calls that overlap on the GPU
 // race on it.
@@ -180,6 +184,16 @@ extern "C" int hweno_stage_batch_static(int n, const hweno_problem* problems, in
         !status[s] || U_out[s] == U_in[s])
       return HWENO_ERR_ARG;
   }
+  // one launch reads every solve's inputs while it writes every solve's outputs: an output
+  // that is another solve's input, base state, first-moment array or output would race
+  for (int s = 0; s < n; ++s)
+    for (int t = 0; t < n; ++t) {
+      const void* o = U_out[s];
+      if (o == U_in[t] || o == Vh[t] || (t != s && (o == U_n[t] || o == U_out[t])) ||
+          (t != s && ((const void*)Vh[s] == U_in[t] || (const void*)Vh[s] == U_n[t] ||
+                      Vh[s] == Vh[t])))
+        return HWENO_ERR_ARG;
+    }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HWENO_ERR_CUDA;
   const int rc = static_device_setup(dev);

@@ -59,15 +59,64 @@ KProblem solve_kproblem(Solve* s);
 
 using namespace hw;
 
+// 1D: block width x threads per cell.  Candidates: 128- and 32-thread blocks of one thread per
+// cell, and for Euler with the characteristic decomposition 128-, 64- and 32-thread blocks of
+// one lane per characteristic field; each timed over eight stage launches (a 1D stage lasts
+// microseconds), the fastest kept.  *best_rows = block width, *best_bands = threads per cell.
+static int tune1d(const hweno_problem* p, Solve* s, cudaStream_t st, int* best_rows,
+                  int* best_bands, double* best_ms) {
+  const bool ch = p->equation == HWENO_EULER && p->characteristic;
+  const int cand[5][2] = {{128, 1}, {32, 1}, {128, 4}, {64, 4}, {32, 4}};
+  const int ncand = ch ? 5 : 2;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const KStage S = solve_stage(s, 1);
+  const KProblem kp = solve_kproblem(s);
+  int rc = HWENO_OK;
+  float best_t = 1e30f;
+  TileShape best;
+  for (int c = 0; c < ncand && rc == HWENO_OK; ++c) {
+    TileShape t;
+    t.width = cand[c][0];
+    t.lanes = cand[c][1];
+    tuning_force_shape1d(t);
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(a, st);
+      cudaError_t e = cudaSuccess;
+      for (int l = 0; l < 8 && e == cudaSuccess; ++l)
+        e = launch_stage1d(p->equation, ch, p->precision == HWENO_MIXED32, kp, S, st);
+      cudaEventRecord(b, st);
+      if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+        rc = HWENO_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0 && ms / 8.f < tmin) tmin = ms / 8.f;
+    }
+    if (rc == HWENO_OK && tmin < best_t) {
+      best_t = tmin;
+      best = t;
+    }
+  }
+  tuning_force_shape1d(TileShape());
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  tuning_set_shape(p->equation, ch ? 1 : 0, p->precision == HWENO_MIXED32, p->nx, 1, best);
+  if (best_rows) *best_rows = best.width;
+  if (best_bands) *best_bands = best.lanes;
+  if (best_ms) *best_ms = best_t;
+  return HWENO_OK;
+}
+
 extern "C" {
 
 int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, int* best_rows,
                    int* best_bands, double* best_ms) {
   if (!e || !p || !host) return HWENO_ERR_ARG;
-  if (p->dim != 2) {
-    engine_set_error(e, "the autotuner covers 2D problems");
-    return HWENO_ERR_ARG;
-  }
   std::lock_guard<std::recursive_mutex> lk(engine_mutex(e));
   cudaSetDevice(engine_device(e));
   Solve* s = nullptr;
@@ -77,6 +126,12 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
   rc = engine_load_state(e, s, host, 0.0, st);
   if (rc) {
     engine_release_solve(e, s);
+    return rc;
+  }
+  if (p->dim == 1) {
+    rc = tune1d(p, s, st, best_rows, best_bands, best_ms);
+    engine_release_solve(e, s);
+    if (rc) engine_set_error(e, "autotune launch failed");
     return rc;
   }
   // candidates: chunk heights (0 = one wave over the resident slots) x band counts (0 = the
@@ -148,11 +203,13 @@ int hweno_tuning_save(const char* path) {
   if (!f) return HWENO_ERR_ARG;
   const std::string dev = device_name();
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  std::fprintf(f, "# hweno tuning table: gpu equation characteristic mixed nx ny rows bands\n");
+  std::fprintf(f, "# hweno tuning table: gpu equation characteristic mixed nx ny rows bands "
+                 "width lanes\n");
   for (auto& kv : g_tune)
-    std::fprintf(f, "%s %d %d %d %d %d %d %d\n", dev.c_str(), std::get<0>(kv.first),
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d\n", dev.c_str(), std::get<0>(kv.first),
                  std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
-                 std::get<4>(kv.first), kv.second.rows, kv.second.bands);
+                 std::get<4>(kv.first), kv.second.rows, kv.second.bands, kv.second.width,
+                 kv.second.lanes);
   std::fclose(f);
   return HWENO_OK;
 }
@@ -168,9 +225,9 @@ int hweno_tuning_load(const char* path) {
     if (line[0] == '#') continue;
     int eq, ch, mx, nx, ny;
     TileShape t;
-    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d", name, &eq, &ch, &mx, &nx, &ny, &t.rows,
-                    &t.bands) == 8 &&
-        dev == name) {
+    const int got = std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d", name, &eq, &ch, &mx,
+                                &nx, &ny, &t.rows, &t.bands, &t.width, &t.lanes);
+    if ((got == 8 || got == 10) && dev == name) {
       tuning_set_shape(eq, ch, mx, nx, ny, t);
       ++n;
     }

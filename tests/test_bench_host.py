@@ -68,6 +68,7 @@ def _fake_binding():
     H.hweno_submit = hweno_submit
     H.hweno_serve = hweno_serve
     H.hweno_poll = hweno_poll
+    H.hweno_autotune = lambda eng, p, U0: (128, 4, 0.01)
     return H
 
 
@@ -78,6 +79,9 @@ def test_tubes_report():
     assert rep["max_rel_diff_batched_vs_plain"] == 0.0
     assert rep["plain_fp64_loop"]["cell_stages_per_s"] > 0
     assert rep["batched"]["cell_stages_per_s"] > 0 and rep["speedup"] > 0
+    single = rep["single_tube"]
+    assert single["default_layout_us_per_step"] > 0
+    assert single["tuned_layout"]["threads_per_cell"] == 4
 
 
 def test_served_stream_report():

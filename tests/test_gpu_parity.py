@@ -41,7 +41,7 @@ def _check_stage(op, hp, k, seed, tol=TOL):
     dt = 0.3 / (alpha[0] / ((op.x1 - op.x0) / op.nx) + (alpha[1] / ((op.y1 - op.y0) / op.ny) if op.dim == 2 else 0.0))
     ref, vref, ost = O.stage(op, k, Uin, Un, Vh if k > 1 else None, alpha, dt)
     got, vgot, a_out, st = gpu_stage(hp, k, Uin, Un, Vh, alpha, dt)
-    assert st == ost   # both sides flag the same non-physical outputs (random data may)
+    assert (st & 1) == ost   # both sides flag the same non-physical outputs (random data may)
     e = rel_err(got, ref, Uin)
     assert e <= tol, f"stage {k}: max rel err {e:.3e}"
     if k == 1:
@@ -230,6 +230,75 @@ def test_mixed_precision_stage(dim):
         a = O.alpha(op, Uin)
         ref, _, ost = O.stage(op, k, Uin, U, vh if k > 1 else None, a, dt)
         got, _, _, st = gpu_stage(hp, k, Uin, U, vh, a, dt)
-        assert st == ost == 0
+        assert (st & 1) == ost == 0
         e = rel_err(got, ref, U)
         assert e <= 1e-5, f"stage {k}: {e:.3e}"
+
+
+@pytest.mark.parametrize("log2z,precision", [(0, H.HWENO_FP64), (110, H.HWENO_FP64),
+                                             (200, H.HWENO_FP64), (-110, H.HWENO_FP64),
+                                             (-200, H.HWENO_FP64), (56, H.HWENO_MIXED32)])
+def test_scaled_data_takes_the_direct_weights_where_the_products_overflow(log2z, precision):
+    """Quadrant + vortex data with rho, rho u, rho v and E scaled by zeta = 2^log2z (velocities
+    unchanged), one stage against the oracle (which always uses the direct formula of Eq.
+    2.22).  Where beta_m u_ave grows like zeta^4, the product of the five d_m = beta_m u_ave
+    + eps leaves the double range once zeta^20 exceeds 2^1023, and the kernel takes the
+    direct formula there: it reports that in the status word's HWENO_STATUS_DIRECT_WEIGHTS bit
+    (set for zeta = 2^56 (FP32 bulk), 2^110, 2^200; clear for 1, 2^-110, 2^-200, where the
+    d_m tend to eps and the product form applies).  The results stay within 1e-12 of the
+    oracle (FP64; FP32 bulk 1e-5)."""
+    w = I.quadrant_vortex_2d(3, 128, window=(0, 40, 128, 30))
+    hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1,
+                        y0=w.y0, y1=w.y1, bc=w.bc, precision=precision)
+    op = _oracle_of(hp)
+    U = w.U0 * 2.0 ** log2z
+    alpha = O.alpha(op, U)
+    dt = 0.3 * ((op.x1 - op.x0) / op.nx) / alpha.sum()
+    ref, vh, ost = O.stage(op, 1, U, U, None, alpha, dt)
+    got, vgot, _, st = gpu_stage(hp, 1, U, U, vh, alpha, dt)
+    # at zeta < 1 epsilon dominates beta_m u_ave, the weights fall back to the linear ones and
+    # the linear scheme oscillates at the quadrant faces: both sides flag the same
+    # non-physical outputs (the scale invariance is one-sided with an absolute epsilon)
+    assert (st & H.HWENO_STATUS_NONPHYSICAL) == ost
+    assert ost == 0 or log2z < 0
+    direct = bool(st & H.HWENO_STATUS_DIRECT_WEIGHTS)
+    assert direct == (log2z >= 56), (log2z, st)
+    tol = TOL if precision == H.HWENO_FP64 else 1e-5
+    assert rel_err(got, ref, U) <= tol
+    assert rel_err(vgot, vh, U) <= tol
+
+
+def test_bounded_wait_returns_timeout_and_the_work_completes():
+    """hweno_set_wait_limit: with the engine's stream held by a bounded busy-wait kernel of
+    about half a second (torch.cuda._sleep, enqueued on that stream by the host), a step with
+    a 20 ms wait limit returns HWENO_ERR_TIMEOUT (here at its first wait, for the solve's time
+    and step count, before it queued its step); nothing queued is cancelled, and after the
+    limit is lifted the engine is consistent: one more step gives the oracle's state after as
+    many steps as the solve has taken (one or two)."""
+    import torch
+    w = I.quadrant_vortex_2d(1, 64)
+    hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=64, ny=64, x0=w.x0, x1=w.x1,
+                        y0=w.y0, y1=w.y1, bc=w.bc)
+    op = _oracle_of(hp)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, w.U0)
+        H.hweno_set_wait_limit(eng, 0.02)
+        st = torch.cuda.ExternalStream(H.hweno_engine_stream(eng))
+        with torch.cuda.stream(st):
+            torch.cuda._sleep(1_000_000_000)        # ~0.5 s of clock cycles, then it ends
+        with pytest.raises(H.HwenoError) as ei:
+            H.hweno_step(eng, sid)
+        assert ei.value.code == H.HWENO_ERR_TIMEOUT
+        H.hweno_set_wait_limit(eng, 0.0)
+        H.hweno_step(eng, sid)
+        got, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        with pytest.raises(H.HwenoError):
+            H.hweno_set_wait_limit(eng, -1.0)
+    finally:
+        H.hweno_destroy(eng)
+    runs = {n: O.run(op, w.U0, 0.0, 1e9, max_steps=n) for n in (1, 2)}
+    n = min(runs, key=lambda k: abs(runs[k][1] - t))
+    U, to, ns, ost = runs[n]
+    assert ost == 0 and t == pytest.approx(to, rel=1e-14)
+    assert rel_err(got, U, w.U0) <= 2e-12

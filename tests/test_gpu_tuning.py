@@ -56,14 +56,17 @@ int main() {
   for (int i = 0; i < n; ++i) {
     s ^= s << 13; s ^= s >> 7; s ^= s << 17;
     double m = 1.0 + (double)(s >> 11) / 9007199254740992.0;      // [1, 2)
-    int e = (int)((s >> 3) % 400) - 200;                           // 2^-200 .. 2^199
+    int e = (int)((s >> 3) % 2098) - 1074;                         // 2^-1074 .. 2^1023
     x[i] = ldexp(m, e) * ((s & 1) ? -1.0 : 1.0);
+    if (i % 1024 == 0) x[i] = (i % 2048 == 0) ? 0.0 : INFINITY;    // division branch
+    if (i % 1024 == 1) x[i] = ldexp(m, -1030);                     // subnormal
   }
   k<<<(n + 255) / 256, 256>>>(x, a, b, n);
   if (cudaDeviceSynchronize() != cudaSuccess) { printf("cuda error\n"); return 2; }
   long long maxulp = 0;
   for (int i = 0; i < n; ++i) {
     long long ua, ub; memcpy(&ua, &a[i], 8); memcpy(&ub, &b[i], 8);
+    if ((ua < 0) != (ub < 0)) { maxulp = 1LL << 60; break; }     // sign mismatch
     long long d = ua > ub ? ua - ub : ub - ua;
     if (d > maxulp) maxulp = d;
   }
@@ -74,8 +77,10 @@ int main() {
 
 
 def test_refined_reciprocal_within_one_ulp_of_division():
-    """rcp_nr (the FP32 reciprocal refined by one third-order step) against CUDA's
-    correctly rounded 1/x on 2^20 values over 2^-200 .. 2^200, both signs."""
+    """rcp_nr (the FP32 reciprocal of the significand refined by one third-order step, the
+    exponent negated on the integer bits; the division for zeros, subnormals, infinities and
+    the largest exponents) against CUDA's correctly rounded 1/x on 2^20 values over the whole
+    double range 2^-1074 .. 2^1024, both signs."""
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "rcp.cu")
         open(src, "w").write(RCP_TEST)
@@ -141,3 +146,60 @@ def test_integer_bit_conversions_equal_the_hardware_conversions():
                        check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
     assert int(out.strip()) == 0
+
+
+# ------------------------------------------------------------------------------------------
+# 1D Euler with the characteristic decomposition: one lane per characteristic field
+def _tuning_file(tmp_path, entries):
+    import torch
+    name = torch.cuda.get_device_name(0).replace(" ", "_")
+    path = str(tmp_path / "t1d.txt")
+    with open(path, "w") as f:
+        for (mixed, nx, width, lanes) in entries:
+            f.write(f"{name} 2 1 {mixed} {nx} 1 0 0 {width} {lanes}\n")
+    return path
+
+
+@pytest.mark.parametrize("width", [32, 64, 128])
+def test_fields_layout_1d_matches_oracle(tmp_path, width):
+    """The lanes-per-field layout (selected through the tuning table) against the oracle at
+    1e-12 for every stage, on grids of one block, one block +- 1 cell, several blocks with a
+    ragged tail, and all boundary conditions."""
+    from gpu_helpers import problems
+    from test_gpu_parity import _check_stage
+    cells = {32: 6, 64: 14, 128: 30}[width]
+    sizes = [2, cells - 1, cells, cells + 1, 3 * cells + 5, 997]
+    sizes = sorted({n for n in sizes if n >= 2})
+    path = _tuning_file(tmp_path, [(0, n, width, 4) for n in sizes])
+    assert H.hweno_tuning_load(path) == len(sizes)
+    try:
+        for n in sizes:
+            for bc in (0, 1, 2):
+                op, hp = problems(1, "euler", n, bc=bc, characteristic=1)
+                for k in (1, 2, 3):
+                    _check_stage(op, hp, k, seed=31 * k + n)
+    finally:
+        H.hweno_tuning_load(_tuning_file(tmp_path, [(0, n, 0, 0) for n in sizes]))
+
+
+def test_autotune_1d_picks_a_layout_and_the_run_matches_oracle():
+    """hweno_autotune on a 1D Euler shock tube (4000 cells): it times the one-thread-per-cell
+    blocks and the lanes-per-field blocks, keeps the fastest, and a run in the kept layout
+    matches the oracle."""
+    w = I.shock_tube_1d(3, n=4000, t_end=0.05)
+    hp = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
+    eng = H.hweno_create()
+    try:
+        width, lanes, ms = H.hweno_autotune(eng, hp, w.U0)
+        assert width in (32, 64, 128) and lanes in (1, 4) and ms > 0.0
+        sid = H.hweno_open(eng, hp, w.U0)
+        ns = H.hweno_advance(eng, sid, 1e9, max_steps=20)
+        got, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+    finally:
+        H.hweno_destroy(eng)
+    import oracle as O
+    op = O.Problem(dim=1, eq=O.EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
+    U, to, nso, st = O.run(op, w.U0, 0.0, 1e9, max_steps=20)
+    assert ns == nso == 20 and st == 0 and t == pytest.approx(to, rel=1e-13)
+    S = np.abs(w.U0[:, 0]).max(axis=(1, 2)).reshape(-1, 1, 1, 1)
+    assert float((np.abs(got - U) / np.maximum(np.abs(U), S)).max()) <= 20e-12
