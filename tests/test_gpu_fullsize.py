@@ -7,6 +7,8 @@ benchmark times.
   evaluated cell by cell (every band and row-chunk edge of the launch geometry, the domain
   corners, and random cells).  The engine's graph-replayed step (what the benchmark times)
   equals the chain of the three stage launches.
+  The same three stages on every cell, against the whole-grid stage of the OpenMP oracle.
+* 200 steps of the same generator at 256^2 through the engine against the oracle's run.
 * 2D Euler 1024^2 (the 200-step production size): stage 1 on sampled cells.
 * The FP32-bulk path at 2048^2: stage 1 on sampled cells within its stated 1e-5 bound.
 * 1D Euler shock tube with 4000 cells: every cell of every stage, and 20 engine steps.
@@ -108,6 +110,51 @@ def euler2048():
     rng = np.random.default_rng(11)
     Vh = rng.uniform(-0.02, 0.02, size=(4, 2, 2048, 2048))
     return w, hp, op, others, Vh
+
+
+def _threads():
+    import os
+    return max(1, os.cpu_count() or 1)
+
+
+def test_2048_fp64_stages_on_every_cell(euler2048):
+    """Stages 1, 2 and 3 at 2048^2 on every cell (and every v-hat / w-hat of stage 1) against
+    the whole-grid oracle stage, run by the OpenMP build on all host cores (bitwise the serial
+    oracle; a few seconds per stage)."""
+    w, hp, op, others, Vh = euler2048
+    a0 = O.alpha(op, w.U0)
+    dt = _cfl_dt(hp, a0)
+    for k, Uin in ((1, w.U0), (2, others[0]), (3, others[1])):
+        alpha = a0 if k == 1 else O.alpha(op, Uin)
+        got, vgot, aout, st = _gpu_stage(hp, k, Uin, w.U0, Vh if k > 1 else np.zeros_like(Vh),
+                                         alpha, dt)
+        ref, vref, ost = O.stage(op, k, Uin, w.U0, Vh if k > 1 else None, alpha, dt,
+                                 threads=_threads())
+        assert st == ost == 0
+        e = rel_err(got, ref, w.U0)
+        assert e <= TOL, f"stage {k}: {e:.3e}"
+        if k == 1:
+            assert rel_err(vgot, vref, w.U0) <= TOL
+        np.testing.assert_allclose(aout, O.alpha(op, ref), rtol=1e-13)
+
+
+def test_200_fp64_steps_match_the_oracle_run():
+    """The 200-step run of the benchmark's generator (quadrant + vortex, seed 0, CFL 0.6) at
+    256^2 through hweno_advance against the OpenMP oracle's 200 steps: the same time, and
+    every cell within 1e-11 of the component scale (the per-stage bound, carried through the
+    600 stages of a run with four quadrant interfaces and their shocks)."""
+    w = I.quadrant_vortex_2d(0, 256)
+    hp, op = _problems(w)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, w.U0)
+        assert H.hweno_advance(eng, sid, 1e9, max_steps=200) == 200
+        got, t = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+    finally:
+        H.hweno_destroy(eng)
+    ref, tr, ns, st = O.run(op, w.U0, 0.0, 1e9, max_steps=200, threads=_threads())
+    assert ns == 200 and st == 0 and t == pytest.approx(tr, rel=1e-13)
+    assert rel_err(got, ref, w.U0) <= 1e-11
 
 
 def test_2048_fp64_stages_on_sampled_cells(euler2048):
