@@ -47,17 +47,17 @@ FP32_PEAK_TFLOPS_FALLBACK = 74.2
 # ncu thread-instruction counts of one 2048^2 launch in its default geometry (22 bands of 94
 # columns, 13 row chunks; profiles/stage2d_euler_2048_instruction_counts.md) per updated
 # cell less the 2.8 % of redundant ring-cell reconstruction: operations (DFMA + DMUL + DADD)
-# 3587 -> 3489.  The FP64 pipe executes one such operation per lane per clock, so its
+# 3562 -> 3465.  The FP64 pipe executes one such operation per lane per clock, so its
 # operation rate is half the FMA flop rate.
-FP64_OPS_PER_CELL_STAGE = 3489.0
+FP64_OPS_PER_CELL_STAGE = 3465.0
 # DRAM bytes read + written by the same launch (ncu)
-FP64_STAGE_DRAM_BYTES = 425.4e6 + 642.9e6
+FP64_STAGE_DRAM_BYTES = 423.1e6 + 657.5e6
 # FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.835
-# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (977 per
+FP64_PIPE_UTIL_NCU = 0.833
+# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (928 per
 # reconstructed cell less 2.9 % ring redundancy at three blocks per SM) and FP32 flops
-FP32BULK_FP64_OPS_PER_CELL_STAGE = 949.0
-FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4168.0
+FP32BULK_FP64_OPS_PER_CELL_STAGE = 902.0
+FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4089.0
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
