@@ -561,6 +561,34 @@ int engine_run(hweno_engine* e, Solve* s, double t_end, long long max_steps,
   const long long limit = max_steps < 0 ? (1LL << 62) : steps0 + max_steps;
   rc = engine_set_target(e, s, t_end, limit, e->stream);
   if (rc) return rc;
+  if (s->prob.dim == 1 && steps1d_supported()) {
+    // 1D: whole steps in one cooperative launch each batch (a 1D stage takes microseconds,
+    // so four launches per step would dominate); the batch grows to the steps left
+    Step1D A;
+    A.P = s->kp;
+    A.sc = s->sc;
+    A.U[0] = s->U0;
+    A.U[1] = s->U1;
+    A.U[2] = s->U2;
+    A.Vh = s->Vh;
+    const bool ch = (s->prob.equation == HWENO_EULER) && s->prob.characteristic;
+    long long batch = 4;
+    for (;;) {
+      CUDA_TRY(e, launch_steps1d(s->prob.equation, ch, s->prob.precision == HWENO_MIXED32, A,
+                                 (int)batch, e->stream));
+      rc = engine_read_scalars(e, s, e->stream);
+      if (rc) return rc;
+      if (s->host->status & kStatusNonphysical) break;
+      if (!(s->host->t < t_end) || s->host->steps >= limit) break;
+      double left = (t_end - s->host->t) / std::max(s->host->dt, 1e-300);
+      long long want = (long long)std::min<double>(left, (double)(limit - s->host->steps));
+      batch = std::max<long long>(1, std::min<long long>(1024, want + 1));
+    }
+    if (steps_taken) *steps_taken = s->host->steps - steps0;
+    if (s->host->status & kStatusNonphysical)
+      return fail(e, HWENO_ERR_NONPHYSICAL, "non-physical state (rho<=0, p<=0 or non-finite)");
+    return HWENO_OK;
+  }
   const int G = 4;  // steps per graph
   rc = ensure_graph(e, s, G);
   if (rc) return rc;

@@ -20,9 +20,10 @@ struct DevScal {
   uint32_t status;
 };
 
-// Start of a time step (one thread): Delta t from the LF speeds of U^n (CFL rule, R8
-// reading) or the fixed step, clipped to t_end; clears the speed slots the three stages
-// raise; sets `active` (0 once t_end, the step limit or a bad status is reached).
+// Start of a time step (one thread): Delta t from the LF speeds of U^n (CFL rule) or the
+// fixed step, clipped to t_end; clears the speed slots the three stages raise; sets `active`
+// (0 once t_end, the step limit or a non-physical state is reached; the informational status
+// bits do not stop the solve).
 __device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_dy, int dim) {
   const double a0 = s->alpha[3][0], a1 = s->alpha[3][1];
   s->alpha[0][0] = a0;
@@ -31,7 +32,7 @@ __device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_
   s->alpha[2][0] = s->alpha[2][1] = 0.0;
   s->alpha[3][0] = s->alpha[3][1] = 0.0;
   const double t = s->t, te = s->t_end;
-  if (!(t < te) || s->steps >= s->step_limit || s->status != 0u) {
+  if (!(t < te) || s->steps >= s->step_limit || (s->status & kStatusNonphysical) != 0u) {
     s->active = 0;
     s->dt = 0.0;
     s->alpha[3][0] = a0;  // the state is unchanged: keep its speeds
@@ -76,6 +77,21 @@ void tuning_set_shape(int eq, int characteristic, int mixed, int nx, int ny, Til
 void tuning_force_shape(TileShape t);
 // The same for 1D launches (block width and threads per cell); all zero = no override.
 void tuning_force_shape1d(TileShape t);
+
+// Device pointers of a 1D solve for the multi-step cooperative launch: U[0] = U^n (stage 3
+// writes it in place), U[1], U[2] the stage buffers, Vh the first-moment modifications.
+struct Step1D {
+  KProblem P;
+  DevScal* sc;
+  double* U[3];
+  double* Vh;
+};
+// Up to nsteps SSP-RK3 steps of a 1D solve in one cooperative launch (fewer when the solve
+// reaches its target); asynchronous on st.  steps1d_supported(): the device can launch
+// cooperative kernels.
+cudaError_t launch_steps1d(int eq, bool characteristic, bool mixed, const Step1D& A,
+                           int nsteps, cudaStream_t st);
+bool steps1d_supported();
 
 // One stage of the modified SSP-RK3 over a whole grid (1D / 2D), asynchronous on st.
 cudaError_t launch_stage1d(int eq, bool characteristic, bool mixed, const KProblem& P,

@@ -6,10 +6,14 @@
 // 128-thread blocks (126 cells each) are used once they give every SM at least one block;
 // shorter grids take one-warp blocks of 30 cells (4000 cells: 134 blocks on 134 SMs instead of
 // 32 blocks on 32 SMs).
+#include <cooperative_groups.h>
+
 #include "launch.h"
 #include "stage1d_item.cuh"
 
 namespace hw {
+
+namespace cg = cooperative_groups;
 
 // 1D shape override of the autotuner (this thread's next launches); zero = none
 static thread_local TileShape g_force1d;
@@ -66,6 +70,97 @@ static cudaError_t launch1d_t(const KProblem& P, const KStage& S, cudaStream_t s
     stage1d_kernel<EQ, CHAR, R, 32><<<(P.nx + 29) / 30, 32, 0, st>>>(P, S);
   }
   return cudaGetLastError();
+}
+
+// Up to nsteps whole SSP-RK3 steps of one 1D solve in one cooperative launch (Eq. 2.13): the
+// step start (dt_update, one thread) and the three stages, each stage an item loop over the
+// same (block width, threads per cell) items as the single-solve launch, separated by grid
+// barriers; the loop ends when dt_update clears `active` (t_end, the step limit, a
+// non-physical state).  Every cell is computed by the same item code as in the per-stage
+// launches, so the results are bitwise those of the graph-replayed steps; a step costs one
+// grid barrier per stage instead of four launches.
+template <int EQ, bool CHAR, typename R, int BW, bool FIELDS>
+__global__ void __launch_bounds__(BW) step1d_coop_kernel(Step1D A, int nsteps, int items) {
+  cg::grid_group grid = cg::this_grid();
+  volatile int* active = &A.sc->active;
+#pragma unroll 1
+  for (int s = 0; s < nsteps; ++s) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) dt_update(A.sc, A.P.inv_dx, A.P.inv_dy, 1);
+    grid.sync();
+    if (*active == 0) return;   // every block reads the same value after the barrier
+#pragma unroll 1
+    for (int k = 1; k <= 3; ++k) {
+      KStage S;
+      S.Uin = A.U[k - 1];
+      S.Un = A.U[0];
+      S.Vh = A.Vh;
+      S.Uout = A.U[k % 3];
+      S.alpha_in = A.sc->alpha[k - 1];
+      S.alpha_out = A.sc->alpha[k];
+      S.dt = &A.sc->dt;
+      S.status = &A.sc->status;
+      S.active = nullptr;
+      S.k = k;
+#pragma unroll 1
+      for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        if constexpr (FIELDS) stage1d_fields_item<R, BW>(A.P, S, it);
+        else stage1d_item<EQ, CHAR, R, BW>(A.P, S, it);
+      }
+      grid.sync();
+    }
+  }
+}
+
+template <int EQ, bool CHAR, typename R, int BW, bool FIELDS>
+static cudaError_t coop_launch(const Step1D& A, int nsteps, int items, cudaStream_t st) {
+  auto kern = step1d_coop_kernel<EQ, CHAR, R, BW, FIELDS>;
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BW, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int blocks = items < per_sm * sm_count() ? items : per_sm * sm_count();
+  Step1D a = A;
+  void* args[] = {&a, &nsteps, &items};
+  return cudaLaunchCooperativeKernel((void*)kern, dim3(blocks), dim3(BW), args, 0, st);
+}
+
+template <int EQ, bool CHAR, typename R>
+static cudaError_t steps1d_t(const Step1D& A, int nsteps, cudaStream_t st) {
+  const int nx = A.P.nx;
+  TileShape ts = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, nx, 1);
+  if constexpr (EQ == EQ_EULER && CHAR) {
+    if (ts.lanes == 4) {
+      const int w = ts.width ? ts.width : 128;
+      if (w == 32) return coop_launch<EQ, CHAR, R, 32, true>(A, nsteps, (nx + 5) / 6, st);
+      if (w == 64) return coop_launch<EQ, CHAR, R, 64, true>(A, nsteps, (nx + 13) / 14, st);
+      return coop_launch<EQ, CHAR, R, 128, true>(A, nsteps, (nx + 29) / 30, st);
+    }
+  }
+  const int wide = (nx + 125) / 126;
+  const int w = ts.width ? ts.width : (wide >= sm_count() ? 128 : 32);
+  if (w == 128) return coop_launch<EQ, CHAR, R, 128, false>(A, nsteps, wide, st);
+  return coop_launch<EQ, CHAR, R, 32, false>(A, nsteps, (nx + 29) / 30, st);
+}
+
+bool steps1d_supported() {
+  int dev = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) return false;
+  return coop != 0;
+}
+
+cudaError_t launch_steps1d(int eq, bool characteristic, bool mixed, const Step1D& A,
+                           int nsteps, cudaStream_t st) {
+  if (eq == EQ_ADV) return mixed ? steps1d_t<EQ_ADV, false, float>(A, nsteps, st)
+                                 : steps1d_t<EQ_ADV, false, double>(A, nsteps, st);
+  if (eq == EQ_BURG) return mixed ? steps1d_t<EQ_BURG, false, float>(A, nsteps, st)
+                                  : steps1d_t<EQ_BURG, false, double>(A, nsteps, st);
+  if (characteristic) return mixed ? steps1d_t<EQ_EULER, true, float>(A, nsteps, st)
+                                   : steps1d_t<EQ_EULER, true, double>(A, nsteps, st);
+  return mixed ? steps1d_t<EQ_EULER, false, float>(A, nsteps, st)
+               : steps1d_t<EQ_EULER, false, double>(A, nsteps, st);
 }
 
 template <int EQ, bool CHAR, typename R>

@@ -245,13 +245,44 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
           };
           // field by field: coefficients, FP64 smoothness indicators and weights (the
           // branch-free product form, the direct formula only where it does not apply),
-          // combination and evaluation
+          // combination and evaluation.  The FP32-bulk class takes the fields in pairs whose
+          // two FP64 weight chains share a basic block (the direct formula, for the rare
+          // cells that need it, after both), which hides part of their latency: 9.10 ms
+          // against 9.20-9.27 ms per 2048^2 stage
+          if constexpr (sizeof(R) == sizeof(double)) {
 #pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            R u[9], v[4], w[4], C[15];
-            field(f, u, v, w);
-            recon2d_coeffs<R, 0>(u, v, w, P, C, fast_weights);
-            evaluate(f, C);
+            for (int f = 0; f < 4; ++f) {
+              R u[9], v[4], w[4], C[15];
+              field(f, u, v, w);
+              recon2d_coeffs<R, 0>(u, v, w, P, C, fast_weights);
+              evaluate(f, C);
+            }
+          } else {
+#pragma unroll
+            for (int f0 = 0; f0 < 4; f0 += 2) {
+              bool ok = true;
+              R C0[15], C1[15];
+              {
+                R u[9], v[4], w[4];
+                field(f0, u, v, w);
+                recon2d_coeffs<R, 1>(u, v, w, P, C0, ok);
+              }
+              {
+                R u[9], v[4], w[4];
+                field(f0 + 1, u, v, w);
+                recon2d_coeffs<R, 1>(u, v, w, P, C1, ok);
+              }
+              if (!ok) {
+                fast_weights = false;
+                R u[9], v[4], w[4];
+                field(f0, u, v, w);
+                recon2d_coeffs<R, 2>(u, v, w, P, C0, ok);
+                field(f0 + 1, u, v, w);
+                recon2d_coeffs<R, 2>(u, v, w, P, C1, ok);
+              }
+              evaluate(f0, C0);
+              evaluate(f0 + 1, C1);
+            }
           }
           R cons[16][4];
 #pragma unroll

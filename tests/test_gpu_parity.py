@@ -302,3 +302,60 @@ def test_bounded_wait_returns_timeout_and_the_work_completes():
     U, to, ns, ost = runs[n]
     assert ost == 0 and t == pytest.approx(to, rel=1e-14)
     assert rel_err(got, U, w.U0) <= 2e-12
+
+
+def test_engine_steps_through_cells_that_need_the_direct_weights():
+    """Data scaled by 2^110: the weights of the non-flat cells take the direct formula and the
+    stages set the informational HWENO_STATUS_DIRECT_WEIGHTS bit.  That bit must not stop the
+    solve: hweno_advance takes every step asked for, with the oracle's time.  At this scale
+    epsilon no longer masks the rounding noise of near-zero characteristic fields (shear and
+    acoustic fields of flat regions), the weights follow that noise, and a 1-ulp change of
+    the data grows to about 1e-7 in five steps in the oracle itself (1e-15 at scale 1); the
+    state is compared within ten times that measured sensitivity."""
+    w = I.quadrant_vortex_2d(3, 128, window=(0, 40, 64, 30))
+    U0 = w.U0 * 2.0 ** 110
+    hp = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=w.nx, ny=w.ny, x0=w.x0, x1=w.x1,
+                        y0=w.y0, y1=w.y1, bc=w.bc)
+    op = _oracle_of(hp)
+    eng = H.hweno_create()
+    try:
+        sid = H.hweno_open(eng, hp, U0)
+        assert H.hweno_advance(eng, sid, 1e9, max_steps=5) == 5
+        got, t = H.hweno_get_state(eng, sid, np.empty_like(U0))
+    finally:
+        H.hweno_destroy(eng)
+    U, to, ns, st = O.run(op, U0, 0.0, 1e9, max_steps=5)
+    assert ns == 5 and st == 0 and t == pytest.approx(to, rel=1e-13)
+    flips = np.random.default_rng(1).choice([-1.0, 0.0, 1.0], size=U0.shape)
+    Up, _, _, _ = O.run(op, U0 * (1.0 + 2.0 ** -52 * flips), 0.0, 1e9, max_steps=5)
+    sens = rel_err(Up, U, U0)
+    assert rel_err(got, U, U0) <= 10.0 * sens + 1e-12, sens
+
+
+@pytest.mark.parametrize("eq,n", [("euler", 400), ("euler", 4000), ("adv", 200), ("burg", 333)])
+def test_1d_advance_in_one_launch_is_bitwise_the_step_by_step_path(eq, n):
+    """hweno_advance runs 1D solves as whole steps in one cooperative launch (grid barriers
+    between the stages); hweno_step launches the step's kernels one by one.  Both run the
+    same per-cell code, so 25 steps give bitwise the same state, time and step count."""
+    if eq == "euler":
+        w = I.shock_tube_1d(4, n=n)
+        hp = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=n, x0=w.x0, x1=w.x1, bc=w.bc)
+    elif eq == "adv":
+        w = I.advection_sine_1d(n)
+        hp = H.make_problem(dim=1, equation=H.HWENO_ADVECTION, nx=n, x0=0.0, x1=2.0, ax=1.0)
+    else:
+        w = I.burgers_sine_1d(n)
+        hp = H.make_problem(dim=1, equation=H.HWENO_BURGERS, nx=n, x0=0.0, x1=2.0)
+    eng = H.hweno_create()
+    try:
+        a = H.hweno_open(eng, hp, w.U0)
+        assert H.hweno_advance(eng, a, 1e9, max_steps=25) == 25
+        ua, ta = H.hweno_get_state(eng, a, np.empty_like(w.U0))
+        b = H.hweno_open(eng, hp, w.U0)
+        for _ in range(25):
+            H.hweno_step(eng, b)
+        ub, tb = H.hweno_get_state(eng, b, np.empty_like(w.U0))
+    finally:
+        H.hweno_destroy(eng)
+    assert ta == tb
+    np.testing.assert_array_equal(ua, ub)
