@@ -44,20 +44,22 @@ ORACLE_FLOPS_STEP_MEAN = (10078.0 + 2 * 10114.0) / 3.0
 FP64_PEAK_TFLOPS_FALLBACK = 1.19
 FP32_PEAK_TFLOPS_FALLBACK = 74.2
 # FP64 arithmetic the fused 2D Euler characteristic kernel executes per cell-stage, from the
-# ncu thread-instruction counts of one 2048^2 launch in its default geometry (22 bands of 94
-# columns, 13 row chunks; profiles/stage2d_euler_2048_instruction_counts.md) per updated
-# cell less the 2.8 % of redundant ring-cell reconstruction: operations (DFMA + DMUL + DADD)
-# 3562 -> 3465.  The FP64 pipe executes one such operation per lane per clock, so its
-# operation rate is half the FMA flop rate.
-FP64_OPS_PER_CELL_STAGE = 3465.0
+# ncu thread-instruction counts of one 2048^2 launch in its default geometry (96-thread
+# blocks, 22 bands of 94 columns, 13 row chunks; profiles/stage2d_euler_2048_instruction_counts.md)
+# per updated cell less the 2.8 % of redundant ring-cell reconstruction: operations (DFMA +
+# DMUL + DADD) 3445 -> 3351.  The FP64 pipe executes one such operation per lane per clock,
+# so its operation rate is half the FMA flop rate.
+FP64_OPS_PER_CELL_STAGE = 3351.0
 # DRAM bytes read + written by the same launch (ncu)
-FP64_STAGE_DRAM_BYTES = 423.1e6 + 657.5e6
+FP64_STAGE_DRAM_BYTES = 422.2e6 + 708.6e6
 # FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.833
+FP64_PIPE_UTIL_NCU = 0.832
 # FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (928 per
-# reconstructed cell less 2.9 % ring redundancy at three blocks per SM) and FP32 flops
+# reconstructed cell less 2.9 % ring redundancy at three blocks per SM), FP32 flops, and the
+# launch's DRAM bytes
 FP32BULK_FP64_OPS_PER_CELL_STAGE = 902.0
-FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 4089.0
+FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 3971.0
+FP32BULK_STAGE_DRAM_BYTES = 463.1e6 + 1052.1e6
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
@@ -353,6 +355,7 @@ def run_ours(args):
                               "fp32_tflops": FP32BULK_FP32_FLOPS_PER_CELL_STAGE * n * n /
                                              (k32_ms / 1e3) / 1e12,
                               "fp32_peak_tflops": peaks["fp32_tflops"],
+                              "traffic": FP32BULK_STAGE_DRAM_BYTES if n == 2048 else None,
                               "peak_note": "FP64 pipe operation rate = half the FMA flop rate "
                                            "measured by hweno_fma_peak in this run"},
                  "l1_vs_fp64": float((diff / scale).mean()),

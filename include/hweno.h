@@ -229,12 +229,14 @@ int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
 
 /* ---- launch-geometry autotuner -------------------------------------------------------- */
 /* Time one fused stage launch of the 2D problem p on a scratch copy of moments_host for each
-   candidate tile shape -- the height of the row chunks a block sweeps (the default one-wave
-   geometry and 8, 16, 32, 64, 128, 256 rows) x the number of bands the columns are split into
-   (the widest bands of at most 126 columns, and 1.25, 1.5 and 2 times as many) -- keep the
-   fastest in the process-wide tuning table (keyed by equation, characteristic decomposition,
-   precision and grid) for every later single-solve launch of such problems, and report it
-   (*best_rows, *best_bands: 0 = the default; *best_ms: one stage).  For a 1D problem the
+   candidate tile shape -- the block width (128, 96 or 64 threads, one per column of a band
+   plus its two ring columns) x the number of bands the columns are split into (the default bands,
+   and 1.25, 1.5 and 2 times as many as the widest bands of that width) x the height of the
+   row chunks a block sweeps (the default one-wave geometry and 8, 16, 32, 64, 128, 256 rows)
+   -- keep the fastest in the process-wide tuning table (keyed by equation, characteristic
+   decomposition, precision and grid) for every later single-solve launch of such problems,
+   and report it (*best_rows, *best_bands: 0 = the default; *best_ms: one stage; the block
+   width through hweno_tuning_query).  For a 1D problem the
    candidates are the block width (128 or 32 threads) and the threads per cell (one per cell,
    or -- Euler with the characteristic decomposition -- one lane per characteristic field in
    blocks of 128, 64 or 32 threads); *best_rows receives the block width and *best_bands the
@@ -247,6 +249,12 @@ int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* mome
    (entries of other GPUs are skipped).  hweno_tuning_load returns the entries loaded. */
 int hweno_tuning_save(const char* path);
 int hweno_tuning_load(const char* path);
+/* The tuning-table entry a single-solve launch of problem p would use: *rows, *bands (2D tile
+   shape; 0 = the default, -1 = the default chosen by the autotuner), *width (block width: 2D
+   128, 96 or 64, 1D 128, 64 or 32; 0 = the default) and *lanes (1D threads per cell).  Returns 1
+   when the table has an entry for p, 0 when not (all outputs 0), HWENO_ERR_ARG for a NULL or
+   malformed p.  Output pointers may be NULL. */
+int hweno_tuning_query(const hweno_problem* p, int* rows, int* bands, int* width, int* lanes);
 
 /* ---------------------------------------------------------------------------------------
  * Measurement utility (no counterpart in the paper).  The FMA throughput of device

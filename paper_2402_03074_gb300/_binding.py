@@ -114,6 +114,9 @@ def lib() -> ctypes.CDLL:
                                           vp, vp, vp], ctypes.c_int),
             "hweno_tuning_save": ([ctypes.c_char_p], ctypes.c_int),
             "hweno_tuning_load": ([ctypes.c_char_p], ctypes.c_int),
+            "hweno_tuning_query": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                                   ctypes.c_int),
             "hweno_fma_peak": ([ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
             "hweno_set_wait_limit": ([E, ctypes.c_double], ctypes.c_int),
         }
@@ -277,6 +280,15 @@ def hweno_tuning_save(path: str) -> None:
 
 def hweno_tuning_load(path: str) -> int:
     return _check(lib().hweno_tuning_load(path.encode()))
+
+
+def hweno_tuning_query(p: hweno_problem):
+    """The tuning-table entry for problem p as a dict (rows, bands, width, lanes), or None."""
+    v = [ctypes.c_int() for _ in range(4)]
+    rc = _check(lib().hweno_tuning_query(ctypes.byref(p), *[ctypes.byref(x) for x in v]))
+    if rc == 0:
+        return None
+    return dict(zip(("rows", "bands", "width", "lanes"), (x.value for x in v)))
 
 
 def hweno_set_wait_limit(eng, seconds: float) -> None:

@@ -6,8 +6,8 @@
 // the unit of the single-solve kernel -- one (band, row chunk) of a 2D solve, one block of
 // kBatchBW - 2 cells of a 1D solve -- so uneven grids share the GPU and the load balances at
 // item granularity.  FP64 and FP32-bulk solves are separate classes (one
-// instantiation each, so every kernel keeps the register and stack footprint of the
-// single-solve kernel).  Every solve keeps its own scalars (dt, t, LF speeds,
+// instantiation each, in the single-solve kernel's default block width, so every kernel
+// keeps the register, shared-memory and stack footprint of the single-solve kernel).  Every solve keeps its own scalars (dt, t, LF speeds,
 // status); one thread per solve advances them at the start of each step, so each solve
 // steps with its own dt.  The work lists live in device memory: admission and retirement
 // rewrite them between steps and the captured step graph stays valid.
@@ -39,7 +39,7 @@ __global__ void batch_dt_kernel(BatchDt* d, BatchCtl* ctl, int nctl) {
 }
 
 template <int EQ, bool CHAR, typename R, int BW>
-__global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
+__global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
     batch_stage_kernel(const BatchSolve* bs, BatchCtl* ctl, int k) {
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];
@@ -135,8 +135,8 @@ static cudaError_t launch_batch1d_t(const BatchSolve* bs, BatchCtl* ctl, int k, 
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t init_batch_t(int* slots_out, size_t* local_out) {
-  constexpr int BW = kBatchBW;
-  const size_t smem = smem_bytes2d<EQ, R, BW>();
+  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
+  const size_t smem = smem_bytes2d<EQ, CHAR, R, BW>();
   auto kern = batch_stage_kernel<EQ, CHAR, R, BW>;
   static int slots = 0;
   static size_t local = 0;
@@ -162,11 +162,11 @@ static cudaError_t init_batch_t(int* slots_out, size_t* local_out) {
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t launch_batch_t(const BatchSolve* bs, BatchCtl* ctl, int k, cudaStream_t st) {
-  constexpr int BW = kBatchBW;
+  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
   int slots = 0;
   cudaError_t e = init_batch_t<EQ, CHAR, R>(&slots, nullptr);
   if (e != cudaSuccess) return e;
-  batch_stage_kernel<EQ, CHAR, R, BW><<<slots, BW, smem_bytes2d<EQ, R, BW>(), st>>>(bs, ctl, k);
+  batch_stage_kernel<EQ, CHAR, R, BW><<<slots, BW, smem_bytes2d<EQ, CHAR, R, BW>(), st>>>(bs, ctl, k);
   return cudaGetLastError();
 }
 
@@ -258,9 +258,9 @@ int batch_slots(int cls) {
 
 void batch_geometry1d(int nx, int* blocks) { *blocks = (nx + (kBatchBW - 2) - 1) / (kBatchBW - 2); }
 
-void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks,
+void batch_geometry(int nx, int ny, int rows, int bw, int* bands, int* wout, int* chunks,
                     bool lane_aware) {
-  split_bands(nx, default_bands(nx, kBatchBW, lane_aware), bands, wout);
+  split_bands(nx, default_bands(nx, bw, lane_aware), bands, wout);
   if (rows < 1) rows = 1;
   *chunks = (ny + rows - 1) / rows;
 }

@@ -7,7 +7,13 @@
 
 namespace hw {
 
-constexpr int kBatchBW = 128;      // threads per block of the batched stage kernels
+constexpr int kBatchBW = 128;      // threads per block of the batched 1D stage kernels
+// threads per block of a class's batched 2D stage kernel: the single-solve default width
+// (96 for characteristic FP64 Euler, whose kernel forms the coefficients once per cell;
+// else 128)
+inline int batch_bw2d(int equation, int characteristic, int mixed) {
+  return default_width2d(equation, equation == EQ_EULER && characteristic != 0, mixed != 0);
+}
 constexpr int kBatchClasses = 16;  // {2D, 1D} x {advection, Burgers, Euler comp.-wise,
                                    // Euler char.} x {FP64, mixed}
 
@@ -40,9 +46,10 @@ struct BatchDt {
 };
 
 int batch_class(int equation, int characteristic, int mixed, int dim = 2);
-// bands (of at most kBatchBW - 2 columns; lane_aware: of at most kBatchBW - 34 columns when
-// that leaves fewer idle lanes, for the FP64 classes) and row chunks of `rows` rows
-void batch_geometry(int nx, int ny, int rows, int* bands, int* wout, int* chunks,
+// bands (of at most bw - 2 columns for blocks of bw threads; lane_aware: of at most bw - 34
+// columns when that leaves fewer idle lanes, for the FP64 classes) and row chunks of `rows`
+// rows
+void batch_geometry(int nx, int ny, int rows, int bw, int* bands, int* wout, int* chunks,
                     bool lane_aware = false);
 void batch_geometry1d(int nx, int* blocks);
 int batch_slots(int cls);  // resident blocks of the class's persistent launch

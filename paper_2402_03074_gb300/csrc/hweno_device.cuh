@@ -453,16 +453,16 @@ __device__ __forceinline__ void combine2d(const R (&c)[15], const R (&u)[9], R a
   for (int n = 3; n < 15; ++n) C[n] = a0 * c[n];
 }
 
-// One field, Steps 1-3: combined monomial coefficients C[15].
+// One field, Steps 2-3 and the combination, from the Appendix coefficients c of p_0 and the
+// averages u[1], u[3], u[4], u[5], u[7] of cells 2, 4, 5, 6, 8 (the other entries of u are
+// not read): combined monomial coefficients C[15].
 // WMODE 0: the weights by nonlinear_weights (product form, direct formula where it does not
 // apply; `ok` cleared where the direct formula was used); 1: the product form alone, without
 // a branch, `ok` cleared where it does not apply (the caller redoes those cells with WMODE 2);
 // 2: the direct formula.
 template <typename R, int WMODE = 0>
-__device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
-                                               const KProblem& P, R (&C)[15], bool& ok) {
-  R c[15];
-  coeffs2d<R>(u, v, w, c);
+__device__ __forceinline__ void recon2d_from_coeffs(const R (&c)[15], const R (&u)[9],
+                                                    const KProblem& P, R (&C)[15], bool& ok) {
   double beta[5], uave;
   beta2d<R>(c, u, beta, uave);
   double a0d, bm[5];
@@ -471,6 +471,15 @@ __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4],
   else nonlinear_weights_direct<5>(beta, uave, P, a0d, bm);
   combine2d<R>(c, u, from_f64<R>(a0d), from_f64<R>(1.0 - a0d), from_f64<R>(bm[1]),
                from_f64<R>(bm[2]), from_f64<R>(bm[3]), from_f64<R>(bm[4]), C);
+}
+// Steps 1-3 of one field from its stencil (u[9] averages, v[4] / w[4] first moments of cells
+// 2, 4, 6, 8).
+template <typename R, int WMODE = 0>
+__device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
+                                               const KProblem& P, R (&C)[15], bool& ok) {
+  R c[15];
+  coeffs2d<R>(u, v, w, c);
+  recon2d_from_coeffs<R, WMODE>(c, u, P, C, ok);
 }
 template <typename R>
 __device__ __forceinline__ void recon2d_coeffs(const R (&u)[9], const R (&v)[4], const R (&w)[4],
@@ -682,16 +691,17 @@ struct Eig1 {
 
 template <typename R>
 struct Eig2 {
+  R vx, vy;                            // velocity of the state
   R un, ut, c, H, q2h, b1h, b2h, hic;  // un: normal velocity, ut: tangential velocity
   R bun, but, hun;                     // b1h un, b1h ut, hic un (shared by every projection)
   R unc, qmH;                          // un c, q2h - H (shared by every unprojection)
   int dir;
-  __device__ __forceinline__ bool init(const KProblem& P, int d, const R* U) {
-    dir = d;
+  // The direction-free part (the state's velocity, sound speed, enthalpy and the scalings of
+  // L), shared by the x and y passes of a cell; then set_dir for the pass.
+  __device__ __forceinline__ bool init_state(const KProblem& P, const R* U) {
     const R ir = rcp<R>(U[0]);
-    const R vx = U[1] * ir, vy = U[2] * ir;
-    un = d == 0 ? vx : vy;
-    ut = d == 0 ? vy : vx;
+    vx = U[1] * ir;
+    vy = U[2] * ir;
     const R gm1 = kconst<R>(P.gm1, P.gm1f);
     q2h = R(0.5) * (vx * vx + vy * vy);
     const R p = gm1 * (U[3] - U[0] * q2h);
@@ -702,24 +712,43 @@ struct Eig2 {
     b1h = R(0.5) * gm1 * (rc * rc);
     b2h = q2h * b1h;
     hic = R(0.5) * rc;
+    qmH = q2h - H;
+    return p > R(0) && U[0] > R(0);
+  }
+  __device__ __forceinline__ void set_dir(int d) {
+    dir = d;
+    un = d == 0 ? vx : vy;
+    ut = d == 0 ? vy : vx;
     bun = b1h * un;
     but = b1h * ut;
     hun = hic * un;
     unc = un * c;
-    qmH = q2h - H;
-    return p > R(0) && U[0] > R(0);
+  }
+  __device__ __forceinline__ bool init(const KProblem& P, int d, const R* U) {
+    const bool ok = init_state(P, U);
+    set_dir(d);
+    return ok;
   }
   // W = L U for all four fields (the terms s and t are shared by the acoustic fields):
   // s = b2h U0 - b1h (un mn + ut mt - U3), t = hic (un U0 - mn)
-  __device__ __forceinline__ void project_all(const R* U, R* W) const {
+  __device__ __forceinline__ void shared_terms(const R* U, R& s, R& t) const {
     const R mn = dir == 0 ? U[1] : U[2];
     const R mt = dir == 0 ? U[2] : U[1];
-    const R s = b2h * U[0] + (b1h * U[3] - but * mt - bun * mn);
-    const R t = hun * U[0] - hic * mn;
+    s = b2h * U[0] + (b1h * U[3] - but * mt - bun * mn);
+    t = hun * U[0] - hic * mn;
+  }
+  __device__ __forceinline__ void project_all(const R* U, R* W) const {
+    R s, t;
+    shared_terms(U, s, t);
+    const R mt = dir == 0 ? U[2] : U[1];
     W[0] = s + t;
     W[1] = U[0] - R(2) * s;
     W[2] = mt - ut * U[0];
     W[3] = s - t;
+  }
+  // field f of L U from the shared terms s, t of U, its density U0 and tangential momentum mt
+  __device__ __forceinline__ R field_of(int f, R s, R t, R U0, R mt) const {
+    return f == 0 ? s + t : (f == 1 ? U0 - R(2) * s : (f == 2 ? mt - ut * U0 : s - t));
   }
   // U = R W (columns u-c, u, shear, u+c in the rotated frame)
   __device__ __forceinline__ void unproject(const R* W, R* U) const {

@@ -161,7 +161,9 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     if (!batched(p) || p->dim != 2) continue;
     const int cls = class_of(p);
     int bands, wout, chunks;
-    batch_geometry(p->nx, p->ny, 1, &bands, &wout, &chunks, p->precision != HWENO_MIXED32);
+    batch_geometry(p->nx, p->ny, 1,
+                   batch_bw2d(p->equation, p->characteristic, p->precision == HWENO_MIXED32),
+                   &bands, &wout, &chunks, p->precision != HWENO_MIXED32);
     cb[cls].push_back(bands);
     cy[cls].push_back(p->ny);
   }
@@ -191,7 +193,8 @@ static int rebuild_lists(Server* S, cudaStream_t st, unsigned* classes) {
     B.mixed = p->precision == HWENO_MIXED32;
     if (p->dim == 2) {
       B.rows = rows_of[cls];
-      batch_geometry(p->nx, p->ny, B.rows, &B.bands, &B.wout, &B.chunks, !B.mixed);
+      batch_geometry(p->nx, p->ny, B.rows, batch_bw2d(p->equation, p->characteristic, B.mixed),
+                     &B.bands, &B.wout, &B.chunks, !B.mixed);
     } else {
       batch_geometry1d(p->nx, &B.bands);
       B.wout = kBatchBW - 2;

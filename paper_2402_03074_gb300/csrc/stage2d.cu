@@ -8,7 +8,7 @@ namespace hw {
 
 // single-solve kernel: one block per (band, chunk)
 template <int EQ, bool CHAR, typename R, int BW>
-__global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
+__global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
     stage2d_kernel(KProblem P, KStage S, int rows, int wout) {
   if (S.active && *S.active == 0) return;
   extern __shared__ double smem[];
@@ -19,10 +19,9 @@ __global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
 static thread_local TileShape g_force_shape;
 void tuning_force_shape(TileShape t) { g_force_shape = t; }
 
-template <int EQ, bool CHAR, typename R>
+template <int EQ, bool CHAR, typename R, int BW>
 static cudaError_t init2d_t(int* slots_out, size_t* local_out) {
-  constexpr int BW = 128;
-  const size_t smem = smem_bytes2d<EQ, R, BW>();
+  const size_t smem = smem_bytes2d<EQ, CHAR, R, BW>();
   auto kern = stage2d_kernel<EQ, CHAR, R, BW>;
   static int slots = 0;  // resident blocks per GPU for this instantiation
   static size_t local = 0;
@@ -46,22 +45,29 @@ static cudaError_t init2d_t(int* slots_out, size_t* local_out) {
   return cudaSuccess;
 }
 
-template <int EQ, bool CHAR, typename R>
-static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
-  constexpr int BW = 128;
+template <int EQ, bool CHAR, typename R, int BW>
+static cudaError_t launch2d_w(const KProblem& P, const KStage& S, TileShape t, cudaStream_t st) {
   int slots = 0;
-  cudaError_t e = init2d_t<EQ, CHAR, R>(&slots, nullptr);
+  cudaError_t e = init2d_t<EQ, CHAR, R, BW>(&slots, nullptr);
   if (e != cudaSuccess) return e;
-  TileShape t = g_force_shape;  // > 0 fixed, -1 default geometry, {0, 0} consult the table
-  if (t.rows == 0 && t.bands == 0)
-    t = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, P.ny);
   // bands of equal width and row chunks filling the resident block slots once, unless the
   // tuning table (or the autotuner) fixes the tile shape (geometry.h)
   const Geom2D g = geom2d(P.nx, P.ny, BW, slots, t.rows > 0 ? t.rows : 0,
                           t.bands > 0 ? t.bands : 0, sizeof(R) == sizeof(double));
   dim3 grid(g.bands, g.chunks);
-  stage2d_kernel<EQ, CHAR, R, BW><<<grid, BW, smem_bytes2d<EQ, R, BW>(), st>>>(P, S, g.rows, g.wout);
+  stage2d_kernel<EQ, CHAR, R, BW><<<grid, BW, smem_bytes2d<EQ, CHAR, R, BW>(), st>>>(P, S, g.rows, g.wout);
   return cudaGetLastError();
+}
+
+template <int EQ, bool CHAR, typename R>
+static cudaError_t launch2d_t(const KProblem& P, const KStage& S, cudaStream_t st) {
+  TileShape t = g_force_shape;  // > 0 fixed, -1 default geometry, {0, 0} consult the table
+  if (t.rows == 0 && t.bands == 0 && t.width == 0)
+    t = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, P.ny);
+  const int w = t.width > 0 ? t.width : default_width2d(EQ, CHAR, sizeof(R) == 4);
+  if (w == 64) return launch2d_w<EQ, CHAR, R, 64>(P, S, t, st);
+  if (w == 96) return launch2d_w<EQ, CHAR, R, 96>(P, S, t, st);
+  return launch2d_w<EQ, CHAR, R, 128>(P, S, t, st);
 }
 
 cudaError_t prepare_stage2d(size_t* max_local) {
@@ -69,7 +75,11 @@ cudaError_t prepare_stage2d(size_t* max_local) {
   cudaError_t e = cudaSuccess;
 #define HW_PREP(EQ, CH, R)                                            \
   if (e == cudaSuccess) {                                             \
-    e = init2d_t<EQ, CH, R>(nullptr, &l);                             \
+    e = init2d_t<EQ, CH, R, 128>(nullptr, &l);                        \
+    m = l > m ? l : m;                                                \
+    if (e == cudaSuccess) e = init2d_t<EQ, CH, R, 96>(nullptr, &l);   \
+    m = l > m ? l : m;                                                \
+    if (e == cudaSuccess) e = init2d_t<EQ, CH, R, 64>(nullptr, &l);   \
     m = l > m ? l : m;                                                \
   }
   HW_PREP(EQ_ADV, false, double) HW_PREP(EQ_ADV, false, float)

@@ -18,11 +18,12 @@ namespace hw {
 
 
 // Resident blocks per SM the 2D stage kernels are compiled for: the FP64 kernels take the
-// whole register file at two blocks per SM (255 registers per thread), the FP32-bulk kernels
-// three (at most 170 registers per thread, a few hundred bytes of spills), which hides more
-// of the FP64 latency of their weight evaluation.
-template <typename R>
-constexpr int kMinBlocks2D = sizeof(R) == 4 ? 3 : 1;
+// whole register file at eight warps per SM (255 registers per thread: two 128-thread or four
+// 64-thread blocks), the FP32-bulk kernels twelve warps (at most 168 registers per thread, a
+// few hundred bytes of spills: three 128-thread or six 64-thread blocks), which hides more of
+// the FP64 latency of their weight evaluation.
+template <typename R, int BW>
+constexpr int kMinBlocks2D = sizeof(R) == 4 ? 384 / BW : (BW == 128 ? 1 : 256 / BW);
 
 // Gauss weights on [-1/2, 1/2] (sum 1) and nodes
 #define GW0 (5.0 / 18.0)
@@ -54,14 +55,30 @@ __device__ __forceinline__ void volume_sum(const KProblem& P, int dir, const R (
 
 // One work item: band `band` (output columns band*wout .. +wout-1) and row chunk `chunk`
 // (output rows chunk*rows .. +rows-1) of one stage of one solve, processed by a whole block.
-// smem: dynamic shared memory of smem_bytes2d<EQ, R, BW>(); red: 2*(BW/32) doubles.
+// smem: dynamic shared memory of smem_bytes2d<EQ, CHAR, R, BW>(); red: 2*(BW/32) doubles.
 // The row window holds the stage input in the bulk precision R (converted once per value
 // when a row is loaded); the FP64 update reads the cell's own averages from global memory
 // when R is float.
-template <int EQ, typename R, int BW>
+//
+// Characteristic FP64 Euler in 96-thread blocks (kCoefOnce): the Appendix coefficients of p_0
+// are linear in the stencil and the projection L is linear, so the coefficients of a field's
+// p_0 are L applied to the coefficient vectors of the conserved components.  Those are formed
+// once per cell for both passes (4 x 64 operations, kept in shared memory: 60 values per
+// thread) and each pass projects the 15 coefficient vectors instead of forming 4 x 15
+// coefficients from 17 projected stencil vectors: 188 fewer FP64 operations per cell.  The
+// extra 46 KB per block fit two blocks per SM at 96 threads (109 KB each), not at 128 (145 KB).
+template <int EQ, bool CHAR, typename R, int BW>
+constexpr bool kCoefOnce = EQ == EQ_EULER && CHAR && sizeof(R) == sizeof(double) && BW == 96;
+
+// Shared memory of a block: the 3-row window, the x-face exchange, the top traces carried
+// from row to row (in shared memory rather than in 48 registers: fewer spills, FP32-bulk
+// stages 2 % faster) and (kCoefOnce) the conserved coefficients.
+template <int EQ, bool CHAR, typename R, int BW>
 constexpr size_t smem_bytes2d() {
   constexpr int NC = (EQ == EQ_EULER) ? 4 : 1;
-  return sizeof(R) * 4 * NC * 3 * (BW + 2) + sizeof(R) * NC * 3 * 2 * BW;
+  return sizeof(R) * 3 * NC * 3 * (BW + 2) + sizeof(R) * NC * 3 * 2 * BW +
+         sizeof(R) * 2 * 3 * NC * BW +
+         (kCoefOnce<EQ, CHAR, R, BW> ? sizeof(R) * NC * 15 * BW : 0);
 }
 
 template <int EQ, bool CHAR, typename R, int BW>
@@ -72,12 +89,23 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   constexpr int NM = 3;
   constexpr int NA = NC * NM;
   constexpr int WC = BW + 2;  // window columns: global columns i0-2 .. i0+BW-1
-  R* win = reinterpret_cast<R*>(smem);                  // [4 rows][NA][WC]
+  // rows r-1, r, r+1 of the stage input for the reconstruction of row r, in slots r mod 3
+  // (row r+2 is loaded into the slot of row r-1 once every thread is done with it)
+  R* win = reinterpret_cast<R*>(smem);                  // [3 rows][NA][WC]
   // x-face exchange, [NC][3][2][BW]: the left trace u and its flux f of every thread's cell;
   // the face flux at the left face of thread x's cell then overwrites the u slot x (its only
   // reader, thread x - 1, has read it by then)
-  R* trL = win + 4 * NA * WC;
+  R* trL = win + 3 * NA * WC;
   auto fhx = [&](int cg, int x) -> R& { return trL[(cg * 2 + 0) * BW + x]; };
+  // top traces of (i, j-1) and g of them, carried to row j: [2][3][NC][BW] (each thread reads
+  // only its own column)
+  R* car = trL + NC * 3 * 2 * BW;
+  auto prevT = [&](int g, int c) -> R& { return car[((0 * 3 + g) * NC + c) * BW + threadIdx.x]; };
+  auto prevTg = [&](int g, int c) -> R& { return car[((1 * 3 + g) * NC + c) * BW + threadIdx.x]; };
+  // kCoefOnce: the Appendix coefficients of the conserved components of the thread's cell,
+  // [component][15][BW] (each thread reads only its own column)
+  R* cco = car + 2 * 3 * NC * BW;
+  (void)cco;
 
   const int nx = P.nx, ny = P.ny;
   const size_t plane = (size_t)nx * ny;
@@ -96,7 +124,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   auto load_row = [&](int r) {
     int fy;
     const int rr = bc_map(r, ny, P.bc[2], P.bc[3], fy);
-    R* dst = win + (r & 3) * NA * WC;
+    R* dst = win + ((r + 3) % 3) * NA * WC;  // r >= -2
     for (int q = t; q < NA * WC; q += BW) {
       const int a = q / WC, col = q - a * WC;
       int fx;
@@ -107,11 +135,10 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
     }
   };
 #pragma unroll 1
-  for (int r = j0 - 2; r <= j0 + 1; ++r) load_row(r);
+  for (int r = j0 - 2; r <= j0; ++r) load_row(r);
   __syncthreads();
 
   // state carried from row j-1 to row j
-  R prevT[3][NC], prevTg[3][NC];   // top traces of (i, j-1) and g of them
   R pend[NC][3];                   // F^1..F^3 of (i, j-1) without its top face
   R pvh[NC], pwh[NC];              // v-hat, w-hat of (i, j-1)
   double wmax0 = 0.0, wmax1 = 0.0;
@@ -119,9 +146,9 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
 
 #pragma unroll 1
   for (int j = j0 - 1; j <= j1; ++j) {
-    const R* wm = win + ((j - 1) & 3) * NA * WC;
-    const R* w0 = win + (j & 3) * NA * WC;
-    const R* wp = win + ((j + 1) & 3) * NA * WC;
+    const R* wm = win + ((j + 2) % 3) * NA * WC;  // j >= -1
+    const R* w0 = win + ((j + 3) % 3) * NA * WC;
+    const R* wp = win + ((j + 4) % 3) * NA * WC;
     auto Wv = [&](int a, int k) -> R {   // moment array a of stencil cell k (0..8)
       const R* rowp = (k < 3) ? wm : (k < 6 ? w0 : wp);
       return rowp[a * WC + t + (k % 3)];
@@ -182,49 +209,36 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
     if constexpr (CHAR && EQ == EQ_EULER) {
       // two characteristic passes (x: edge points of the x faces, f-volume, v-hat; y: edge
       // points of the y faces, g-volume, w-hat); the x faces are formed between them so the
-      // x-pass results are dead during the y pass
+      // x-pass results are dead during the y pass.  The eigenvector state is shared.
+      Eig2<R> E;
+      if (need) {
+        R U5[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) U5[c] = Wv(c * NM, 4);
+        E.init_state(P, U5);
+        if constexpr (kCoefOnce<EQ, CHAR, R, BW>) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            R u[9], v[4], w[4], cf[15];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) u[k] = Wv(c * NM, k);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              v[e] = Wv(c * NM + 1, 2 * e + 1);
+              w[e] = Wv(c * NM + 2, 2 * e + 1);
+            }
+            coeffs2d<R>(u, v, w, cf);
+#pragma unroll
+            for (int n = 0; n < 15; ++n) cco[(c * 15 + n) * BW + t] = cf[n];
+          }
+        }
+      }
 #pragma unroll
       for (int pass = 0; pass < 2; ++pass) {
         if (pass == 0 && !xrow) continue;
         if (need) {
-          R U5[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) U5[c] = Wv(c * NM, 4);
-          Eig2<R> E;
-          E.init(P, pass, U5);
+          E.set_dir(pass);
           R ch[16][4];  // characteristic values: 6 edge points, 9 interior, modification
-          // the stencil in characteristic variables, all four fields at once: 9 averages and
-          // the x / y first moments of cells 2, 4, 6, 8
-          R Wu[9][4], Wv_[4][4], Ww[4][4];
-#pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            R Uk[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) Uk[c] = Wv(c * NM, k);
-            E.project_all(Uk, Wu[k]);
-          }
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int k = 2 * e + 1;
-            R Vk[4], Zk[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              Vk[c] = Wv(c * NM + 1, k);
-              Zk[c] = Wv(c * NM + 2, k);
-            }
-            E.project_all(Vk, Wv_[e]);
-            E.project_all(Zk, Ww[e]);
-          }
-          // one field's stencil in characteristic variables
-          auto field = [&](int f, R (&u)[9], R (&v)[4], R (&w)[4]) {
-#pragma unroll
-            for (int k = 0; k < 9; ++k) u[k] = Wu[k][f];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              v[e] = Wv_[e][f];
-              w[e] = Ww[e][f];
-            }
-          };
           // the combined polynomial of field f -> its points and modification
           auto evaluate = [&](int f, const R (&C)[15]) {
             R ea[3], eb[3], in[9];
@@ -243,45 +257,116 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
 #pragma unroll
             for (int p = 0; p < 9; ++p) ch[6 + p][f] = in[p];
           };
-          // field by field: coefficients, FP64 smoothness indicators and weights (the
-          // branch-free product form, the direct formula only where it does not apply),
-          // combination and evaluation.  The FP32-bulk class takes the fields in pairs whose
-          // two FP64 weight chains share a basic block (the direct formula, for the rare
-          // cells that need it, after both), which hides part of their latency: 9.10 ms
-          // against 9.20-9.27 ms per 2048^2 stage
-          if constexpr (sizeof(R) == sizeof(double)) {
+          if constexpr (kCoefOnce<EQ, CHAR, R, BW>) {
+            // the shared projection terms of the 15 coefficient vectors, and the averages of
+            // cells 2, 4, 5, 6, 8 (u_ave, the linear polynomials) in characteristic variables
+            const int tang = pass == 0 ? 2 : 1;  // tangential momentum component
+            R cs[15], ct[15];
+#pragma unroll
+            for (int n = 0; n < 15; ++n) {
+              R Uc[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) Uc[c] = cco[(c * 15 + n) * BW + t];
+              E.shared_terms(Uc, cs[n], ct[n]);
+            }
+            R Wa[5][4];
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+              const int k = e == 0 ? 1 : (e == 4 ? 7 : e + 2);  // cells 2, 4, 5, 6, 8
+              R Uk[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) Uk[c] = Wv(c * NM, k);
+              E.project_all(Uk, Wa[e]);
+            }
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-              R u[9], v[4], w[4], C[15];
-              field(f, u, v, w);
-              recon2d_coeffs<R, 0>(u, v, w, P, C, fast_weights);
+              R cf[15], u[9], C[15];
+#pragma unroll
+              for (int n = 0; n < 15; ++n)
+                cf[n] = E.field_of(f, cs[n], ct[n], cco[n * BW + t],
+                                   cco[(tang * 15 + n) * BW + t]);
+              u[0] = u[2] = u[6] = u[8] = R(0);
+              u[1] = Wa[0][f];
+              u[3] = Wa[1][f];
+              u[4] = Wa[2][f];
+              u[5] = Wa[3][f];
+              u[7] = Wa[4][f];
+              recon2d_from_coeffs<R, 0>(cf, u, P, C, fast_weights);
               evaluate(f, C);
             }
           } else {
+            // the stencil in characteristic variables, all four fields at once: 9 averages
+            // and the x / y first moments of cells 2, 4, 6, 8
+            R Wu[9][4], Wv_[4][4], Ww[4][4];
 #pragma unroll
-            for (int f0 = 0; f0 < 4; f0 += 2) {
-              bool ok = true;
-              R C0[15], C1[15];
-              {
-                R u[9], v[4], w[4];
-                field(f0, u, v, w);
-                recon2d_coeffs<R, 1>(u, v, w, P, C0, ok);
+            for (int k = 0; k < 9; ++k) {
+              R Uk[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) Uk[c] = Wv(c * NM, k);
+              E.project_all(Uk, Wu[k]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int k = 2 * e + 1;
+              R Vk[4], Zk[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                Vk[c] = Wv(c * NM + 1, k);
+                Zk[c] = Wv(c * NM + 2, k);
               }
-              {
-                R u[9], v[4], w[4];
-                field(f0 + 1, u, v, w);
-                recon2d_coeffs<R, 1>(u, v, w, P, C1, ok);
+              E.project_all(Vk, Wv_[e]);
+              E.project_all(Zk, Ww[e]);
+            }
+            // one field's stencil in characteristic variables
+            auto field = [&](int f, R (&u)[9], R (&v)[4], R (&w)[4]) {
+#pragma unroll
+              for (int k = 0; k < 9; ++k) u[k] = Wu[k][f];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                v[e] = Wv_[e][f];
+                w[e] = Ww[e][f];
               }
-              if (!ok) {
-                fast_weights = false;
-                R u[9], v[4], w[4];
-                field(f0, u, v, w);
-                recon2d_coeffs<R, 2>(u, v, w, P, C0, ok);
-                field(f0 + 1, u, v, w);
-                recon2d_coeffs<R, 2>(u, v, w, P, C1, ok);
+            };
+            // field by field: coefficients, FP64 smoothness indicators and weights (the
+            // branch-free product form, the direct formula only where it does not apply),
+            // combination and evaluation.  The FP32-bulk class takes the fields in pairs whose
+            // two FP64 weight chains share a basic block (the direct formula, for the rare
+            // cells that need it, after both), which hides part of their latency: 9.10 ms
+            // against 9.20-9.27 ms per 2048^2 stage
+            if constexpr (sizeof(R) == sizeof(double)) {
+#pragma unroll
+              for (int f = 0; f < 4; ++f) {
+                R u[9], v[4], w[4], C[15];
+                field(f, u, v, w);
+                recon2d_coeffs<R, 0>(u, v, w, P, C, fast_weights);
+                evaluate(f, C);
               }
-              evaluate(f0, C0);
-              evaluate(f0 + 1, C1);
+            } else {
+#pragma unroll
+              for (int f0 = 0; f0 < 4; f0 += 2) {
+                bool ok = true;
+                R C0[15], C1[15];
+                {
+                  R u[9], v[4], w[4];
+                  field(f0, u, v, w);
+                  recon2d_coeffs<R, 1>(u, v, w, P, C0, ok);
+                }
+                {
+                  R u[9], v[4], w[4];
+                  field(f0 + 1, u, v, w);
+                  recon2d_coeffs<R, 1>(u, v, w, P, C1, ok);
+                }
+                if (!ok) {
+                  fast_weights = false;
+                  R u[9], v[4], w[4];
+                  field(f0, u, v, w);
+                  recon2d_coeffs<R, 2>(u, v, w, P, C0, ok);
+                  field(f0 + 1, u, v, w);
+                  recon2d_coeffs<R, 2>(u, v, w, P, C1, ok);
+                }
+                evaluate(f0, C0);
+                evaluate(f0 + 1, C1);
+              }
             }
           }
           R cons[16][4];
@@ -374,7 +459,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
       for (int g = 0; g < 3; ++g)
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-          gh[g][c] = prevTg[g][c] + ybg[g][c] - a2 * (yb[g][c] - prevT[g][c]);  // 2 x LF flux
+          gh[g][c] = prevTg(g, c) + ybg[g][c] - a2 * (yb[g][c] - prevT(g, c));  // 2 x LF flux
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const R sw = R(0.5 * GW0) * (gh[0][c] + gh[2][c]) + R(0.5 * GW1) * gh[1][c];
@@ -456,8 +541,8 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
         flux_dir<EQ, R>(P, 1, yt[g], tg);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          prevT[g][c] = yt[g][c];
-          prevTg[g][c] = tg[c];
+          prevT(g, c) = yt[g][c];
+          prevTg(g, c) = tg[c];
         }
       }
 #pragma unroll
@@ -470,7 +555,7 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
       }
     }
     __syncthreads();                       // every read of row j-1 is done
-    if (j + 3 <= j1 + 1) load_row(j + 3);  // into the slot of row j-1
+    if (j + 2 <= j1 + 1) load_row(j + 2);  // into the slot of row j-1
     __syncthreads();
   }
 

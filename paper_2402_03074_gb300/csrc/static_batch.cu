@@ -59,7 +59,7 @@ __global__ void static_setup_kernel(StaticScratch* dst, StaticScratch src) {
 }
 
 template <int EQ, bool CHAR, typename R, int BW>
-__global__ void __launch_bounds__(BW, kMinBlocks2D<R>)
+__global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
     static_batch_kernel(StaticScratch* sc, int k) {
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];
@@ -108,9 +108,9 @@ static bool g_static_ready[64];
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t static_class_setup(int* slots, size_t* local) {
-  constexpr int BW = kBatchBW;
+  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
   auto kern = static_batch_kernel<EQ, CHAR, R, BW>;
-  const size_t smem = smem_bytes2d<EQ, R, BW>();
+  const size_t smem = smem_bytes2d<EQ, CHAR, R, BW>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
@@ -128,8 +128,8 @@ static cudaError_t static_class_setup(int* slots, size_t* local) {
 
 template <int EQ, bool CHAR, typename R>
 static void static_launch(int slots, StaticScratch* ptr, int k, cudaStream_t st) {
-  constexpr int BW = kBatchBW;
-  static_batch_kernel<EQ, CHAR, R, BW><<<slots, BW, smem_bytes2d<EQ, R, BW>(), st>>>(ptr, k);
+  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
+  static_batch_kernel<EQ, CHAR, R, BW><<<slots, BW, smem_bytes2d<EQ, CHAR, R, BW>(), st>>>(ptr, k);
 }
 
 // set-up of one device (the current one): scratch address and every class's launch setup
@@ -212,7 +212,10 @@ extern "C" int hweno_stage_batch_static(int n, const hweno_problem* problems, in
   int bands[HWENO_STATIC_BATCH_MAX], wout[HWENO_STATIC_BATCH_MAX], chunks[HWENO_STATIC_BATCH_MAX];
   int nys[HWENO_STATIC_BATCH_MAX];
   for (int s = 0; s < n; ++s) {
-    batch_geometry(problems[s].nx, problems[s].ny, 1, &bands[s], &wout[s], &chunks[s]);
+    batch_geometry(problems[s].nx, problems[s].ny, 1,
+                   batch_bw2d(problems[s].equation, problems[s].characteristic,
+                              problems[s].precision == HWENO_MIXED32),
+                   &bands[s], &wout[s], &chunks[s]);
     nys[s] = problems[s].ny;
   }
   const int rows = batch_rows(bands, nys, n, D.slots[cls]);

@@ -1,14 +1,16 @@
 // tune.cu -- launch-geometry autotuner and its tuning table.
 //
 // The 2D stage kernel's blocks sweep row chunks of a band.  The tile shape trades redundant
-// work against balance: taller chunks waste fewer ring rows, narrower bands more ring
-// columns and lanes, while the tile count sets how evenly the blocks fill the SMs.  The
-// autotuner times one stage launch of a problem for each candidate shape (chunk height x
-// band count) on a scratch copy of the caller's moments, keeps the fastest in a process-wide
-// table keyed by (equation, characteristic decomposition, precision, grid), and the table is
-// consulted by every later single-solve launch of such a problem (the batched launches size
-// their work items from the load instead).  The table can be saved and loaded as text;
-// entries carry the GPU name.
+// work against balance and latency hiding: taller chunks waste fewer ring rows, narrower
+// bands more ring columns and lanes, the tile count sets how evenly the blocks fill the SMs,
+// and the block width (64, 96 or 128 threads) sets the resident warps per SM and the idle
+// lanes of a band (the 96-thread characteristic FP64 kernel also forms the coefficients once
+// per cell).  The autotuner times one stage launch of a problem for each candidate shape
+// (block width x band count x chunk height) on a scratch copy of the caller's moments, keeps
+// the fastest in a process-wide table keyed by (equation, characteristic decomposition,
+// precision, grid), and the table is consulted by every later single-solve launch of such a
+// problem (the batched launches size their work items from the load instead).  The table can
+// be saved and loaded as text; entries carry the GPU name.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -134,11 +136,11 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
     if (rc) engine_set_error(e, "autotune launch failed");
     return rc;
   }
-  // candidates: chunk heights (0 = one wave over the resident slots) x band counts (0 = the
-  // widest bands of at most 126 columns; then 1.25, 1.5 and 2 times as many)
+  // candidates: block widths (128, 96 and 64 threads) x band counts (0 = the default bands; then
+  // 1.25, 1.5 and 2 times as many as the widest bands) x chunk heights (0 = one wave over the
+  // resident slots)
   const int rows_c[] = {0, 8, 16, 32, 64, 128, 256};
-  const int bmin = (p->nx + 125) / 126;
-  int bands_c[4] = {0, (5 * bmin + 3) / 4, (3 * bmin + 1) / 2, 2 * bmin};
+  const int widths[] = {128, 96, 64};
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
@@ -146,35 +148,42 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
   float best_t = 1e30f;
   const KStage S = solve_stage(s, 1);
   const KProblem kp = solve_kproblem(s);
-  for (int bi = 0; bi < 4 && rc == HWENO_OK; ++bi) {
-    const int bc = bands_c[bi];
-    if (bi > 0 && (bc <= bmin || bc > p->nx || bc == bands_c[bi - 1])) continue;
-    for (int r : rows_c) {
-      if (r > 0 && r >= p->ny && r != rows_c[1]) continue;
-      TileShape t;
-      t.rows = r > 0 ? r : -1;
-      t.bands = bc > 0 ? bc : -1;
-      tuning_force_shape(t);
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 4; ++rep) {
-        cudaEventRecord(a, st);
-        cudaError_t c = launch_stage2d(p->equation,
-                                       p->equation == HWENO_EULER && p->characteristic,
-                                       p->precision == HWENO_MIXED32, kp, S, st);
-        cudaEventRecord(b, st);
-        if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
-          rc = HWENO_ERR_CUDA;
-          break;
+  for (int wi = 0; wi < 3 && rc == HWENO_OK; ++wi) {
+    const int bw = widths[wi];
+    const int bmin = (p->nx + bw - 3) / (bw - 2);
+    const int bands_c[4] = {0, (5 * bmin + 3) / 4, (3 * bmin + 1) / 2, 2 * bmin};
+    for (int bi = 0; bi < 4 && rc == HWENO_OK; ++bi) {
+      const int bc = bands_c[bi];
+      if (bi > 0 && (bc <= bmin || bc > p->nx || bc == bands_c[bi - 1])) continue;
+      for (int r : rows_c) {
+        if (r > 0 && r >= p->ny && r != rows_c[1]) continue;
+        TileShape t;
+        t.rows = r > 0 ? r : -1;
+        t.bands = bc > 0 ? bc : -1;
+        t.width = bw;
+        tuning_force_shape(t);
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(a, st);
+          cudaError_t c = launch_stage2d(p->equation,
+                                         p->equation == HWENO_EULER && p->characteristic,
+                                         p->precision == HWENO_MIXED32, kp, S, st);
+          cudaEventRecord(b, st);
+          if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
+            rc = HWENO_ERR_CUDA;
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          if (rep > 0 && ms < tmin) tmin = ms;
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (rep > 0 && ms < tmin) tmin = ms;
-      }
-      if (rc) break;
-      if (tmin < best_t) {
-        best_t = tmin;
-        best.rows = r;
-        best.bands = bc;
+        if (rc) break;
+        if (tmin < best_t) {
+          best_t = tmin;
+          best.rows = r;
+          best.bands = bc;
+          best.width = bw;
+        }
       }
     }
   }
@@ -189,12 +198,25 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
   TileShape keep;
   keep.rows = best.rows > 0 ? best.rows : -1;
   keep.bands = best.bands > 0 ? best.bands : -1;
+  keep.width = best.width;
   tuning_set_shape(p->equation, p->equation == HWENO_EULER ? p->characteristic : 0,
                    p->precision == HWENO_MIXED32, p->nx, p->ny, keep);
   if (best_rows) *best_rows = best.rows;
   if (best_bands) *best_bands = best.bands;
   if (best_ms) *best_ms = best_t;
   return HWENO_OK;
+}
+
+int hweno_tuning_query(const hweno_problem* p, int* rows, int* bands, int* width, int* lanes) {
+  if (!p || (p->dim != 1 && p->dim != 2)) return HWENO_ERR_ARG;
+  const int ch = p->equation == HWENO_EULER ? p->characteristic : 0;
+  const TileShape t = tuning_shape(p->equation, ch, p->precision == HWENO_MIXED32, p->nx,
+                                   p->dim == 1 ? 1 : p->ny);
+  if (rows) *rows = t.rows;
+  if (bands) *bands = t.bands;
+  if (width) *width = t.width;
+  if (lanes) *lanes = t.lanes;
+  return (t.rows | t.bands | t.width | t.lanes) ? 1 : 0;
 }
 
 int hweno_tuning_save(const char* path) {

@@ -48,3 +48,21 @@ def rel_err(got, ref, U_scale):
     S = np.abs(U_scale[:, 0]).max(axis=(1, 2))
     S = S.reshape((-1,) + (1,) * (ref.ndim - 1))
     return float((np.abs(got - ref) / np.maximum(np.abs(ref), S)).max())
+
+
+def gpu_problems_stage(nx, ny, characteristic, mixed, seed, k=2):
+    """Stage k of 2D Euler on seeded smooth-plus-noise data (transmissive) through
+    hweno_stage_device; returns the output moments."""
+    rng = np.random.default_rng(seed)
+    op, hp = problems(2, "euler", nx, ny, bc=1, characteristic=characteristic,
+                      precision=H.HWENO_MIXED32 if mixed else H.HWENO_FP64)
+    U = np.zeros((4, 3, ny, nx))
+    U[0, 0] = 1.0 + 0.2 * rng.random((ny, nx))
+    U[1, 0] = 0.3 * rng.standard_normal((ny, nx))
+    U[2, 0] = 0.3 * rng.standard_normal((ny, nx))
+    U[3, 0] = 2.5 + 0.5 * rng.random((ny, nx))
+    U[:, 1:] = 0.01 * rng.standard_normal((4, 2, ny, nx))
+    Un = U + 1e-3 * rng.standard_normal(U.shape)
+    Vh = 0.01 * rng.standard_normal((4, 2, ny, nx))
+    out, _, _, _ = gpu_stage(hp, k, U, Un, Vh, (2.0, 2.0), 1e-3)
+    return out

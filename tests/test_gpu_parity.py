@@ -67,9 +67,11 @@ def test_stage_2d(eq, bc, ch, k):
     _check_stage(op, hp, k, seed=20 * k)
 
 
-@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (126, 3), (127, 4), (128, 9), (252, 2)])
+@pytest.mark.parametrize("nx,ny", [(2, 2), (3, 5), (93, 4), (94, 3), (95, 4), (126, 3),
+                                   (127, 4), (128, 9), (188, 5), (189, 2), (252, 2)])
 def test_stage_2d_edge_sizes(nx, ny):
-    """Grids of 2 cells, band-width multiples and +-1, single-row chunks."""
+    """Grids of 2 cells, band-width multiples and +-1 (bands of at most 94 columns in 96-thread
+    blocks, 126 in 128-thread blocks), single-row chunks."""
     op, hp = problems(2, "euler", nx, ny, bc=1)
     _check_stage(op, hp, 1, seed=5)
     _check_stage(op, hp, 2, seed=6)
