@@ -146,8 +146,11 @@ int hweno_conservation(hweno_engine* eng, uint64_t id, double* sums, double* abs
    has rho <= 0, p <= 0 or non-finite values (the state is kept as computed). */
 int hweno_step(hweno_engine* eng, uint64_t id, double* dt_taken);
 /* Steps until t == t_end (the last step is clipped to land on t_end) or max_steps steps
-   (max_steps < 0: no limit).  The step loop runs as replays of a captured CUDA graph with
-   no host round trip per step; the status word is checked between batches of steps. */
+   (max_steps < 0: no limit), with no host round trip per step: 2D solves replay a captured
+   CUDA graph of four steps; 1D solves run batches of whole steps in one launch (a grid of at
+   most 16 x 30 cells resident in one thread-block cluster, longer grids in a cooperative
+   launch), bitwise the results of hweno_step.  The status word is checked between batches of
+   steps. */
 int hweno_advance(hweno_engine* eng, uint64_t id, double t_end, int64_t max_steps,
                   int64_t* steps_taken);
 /* Free a solve. */

@@ -111,6 +111,173 @@ __global__ void __launch_bounds__(BW) step1d_coop_kernel(Step1D A, int nsteps, i
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Short 1D solves resident in one thread-block cluster.  A grid of at most kClusterW times the
+// cluster size cells (30 cells per one-warp CTA, clusters of up to 8 CTAs, 16 where the device
+// allows) lives in the CTAs' shared memory for the whole launch: CTA r owns cells
+// [30 r, 30 r + 30) with their U^n, U^(1), U^(2) and V-hat.  Each stage fills the item's
+// window from the owners' shared memory through distributed shared memory (DSMEM), runs the
+// same per-cell code as the per-stage launches (stage1d_item_io), and writes its own cells;
+// the stages are separated by cluster barriers (0.27 us on a GB300, against 1.4 us for a grid
+// barrier), and the LF speed and the non-physical flag of a stage are reduced by every CTA from
+// the CTAs' shared slots after the barrier, so every CTA steps with the same alpha and dt.  The
+// results are bitwise those of the per-stage launches.
+constexpr int kClusterW = 30;  // cells per one-warp CTA
+
+template <int NA, int W>
+struct Cluster1D {
+  double (*st)[NA][W];   // this CTA's [3] stage buffers (U^n, U^(1), U^(2)) of its cells
+  double (*vhs)[W];      // this CTA's V-hat of its cells
+  double* amax;          // this CTA's maximum output speed of the stage
+  unsigned* bad;         // this CTA's non-physical flag of the stage
+  int kin, kout, kk, i0;
+  double dtv, alphav;
+  __device__ __forceinline__ double in(int a, int i) const {
+    const int owner = i / W;
+    cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+    const double* src = cl.map_shared_rank(&st[kin][a][0], owner);
+    return src[i - owner * W];
+  }
+  __device__ __forceinline__ double un(int a, int i) const { return st[0][a][i - i0]; }
+  __device__ __forceinline__ double vh(int c, int i) const { return vhs[c][i - i0]; }
+  __device__ __forceinline__ void set_vh(int c, int i, double v) const { vhs[c][i - i0] = v; }
+  __device__ __forceinline__ void out(int a, int i, double v) const { st[kout][a][i - i0] = v; }
+  __device__ __forceinline__ double dt() const { return dtv; }
+  __device__ __forceinline__ double alpha() const { return alphav; }
+  __device__ __forceinline__ int k() const { return kk; }
+  __device__ __forceinline__ void nonphysical() const { *bad = 1u; }
+  __device__ __forceinline__ void raise_alpha(double m) const { *amax = m; }
+};
+
+// The stage-k slots of every CTA of the cluster -> the solve's alpha of the stage output and
+// its non-physical bit (the same values as the per-stage launches' atomic maximum and OR):
+// lane r of the CTA's warp reads CTA r's slots, a warp reduction combines them, lane 0 keeps
+// the result.  nb <= 16 < 32.
+__device__ __forceinline__ void cluster_reduce(DevScal& sc, double (*amax)[1], unsigned (*bad)[1],
+                                               int k, int nb) {
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  const int t = threadIdx.x;
+  double v = 0.0;
+  unsigned b = 0u;
+  if (t < nb) {
+    v = cl.map_shared_rank(&amax[k][0], t)[0];
+    if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000LL);  // NaN -> +inf
+    b = cl.map_shared_rank(&bad[k][0], t)[0];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    b |= __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (t == 0) {
+    sc.alpha[k][0] = fmax(sc.alpha[k][0], v);
+    if (b) sc.status |= kStatusNonphysical;
+  }
+}
+
+template <int EQ, bool CHAR, typename R>
+__global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps) {
+  constexpr int BW = 32, W = kClusterW, NC = (EQ == EQ_EULER) ? 3 : 1, NA = NC * 2;
+  static_assert(W == BW - 2, "one thread per reconstructed cell");
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double st[3][NA][W];
+  __shared__ double vhs[NC][W];
+  __shared__ double amax[4][1];   // [k]: this CTA's maximum output speed of stage k
+  __shared__ unsigned bad[4][1];  // [k]: this CTA's non-physical flag of stage k
+  __shared__ DevScal scl;         // the solve's scalars (every CTA holds the same values)
+  const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks();
+  const int nx = A.P.nx, i0 = rank * W, t = threadIdx.x;
+  for (int q = t; q < NA * W; q += BW) {
+    const int a = q / W, j = q - a * W;
+    st[0][a][j] = (i0 + j < nx) ? A.U[0][(size_t)a * nx + i0 + j] : 0.0;
+  }
+  if (t == 0) {
+    scl = *A.sc;
+    for (int k = 0; k < 4; ++k) {
+      amax[k][0] = 0.0;
+      bad[k][0] = 0u;
+    }
+  }
+#pragma unroll 1
+  for (int s = 0;; ++s) {
+    cl.sync();  // stage 3 of the previous step is complete in every CTA
+    if (s > 0) cluster_reduce(scl, amax, bad, 3, nb);
+    if (t == 0 && s < nsteps) dt_update(&scl, A.P.inv_dx, A.P.inv_dy, 1);
+    __syncthreads();
+    if (s == nsteps || scl.active == 0) break;  // the same decision in every CTA
+#pragma unroll 1
+    for (int k = 1; k <= 3; ++k) {
+      if (k > 1) {
+        cl.sync();  // stage k-1 is complete in every CTA
+        cluster_reduce(scl, amax, bad, k - 1, nb);
+        __syncthreads();
+      }
+      Cluster1D<NA, W> io{st, vhs, &amax[k][0], &bad[k][0], k - 1, k % 3, k, i0,
+                          scl.dt, scl.alpha[k - 1][0]};
+      if (t == 0) bad[k][0] = 0u;
+      stage1d_item_io<EQ, CHAR, R, BW>(A.P, io, rank);
+    }
+  }
+  for (int q = t; q < NA * W; q += BW) {
+    const int a = q / W, j = q - a * W;
+    if (i0 + j < nx) A.U[0][(size_t)a * nx + i0 + j] = st[0][a][j];
+  }
+  if (rank == 0 && t == 0) *A.sc = scl;
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// Largest cluster (CTAs) the device runs for this kernel: 16 where non-portable cluster sizes
+// are allowed and a 16-CTA cluster fits, else 8; 0 if clusters are not available.
+template <int EQ, bool CHAR, typename R>
+static int cluster_max() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cache[dev] != 0) return cache[dev] > 0 ? cache[dev] : 0;
+  int cc = 0;
+  cudaDeviceGetAttribute(&cc, cudaDevAttrComputeCapabilityMajor, dev);
+  int best = -1;
+  if (cc >= 9) {
+    auto kern = step1d_cluster_kernel<EQ, CHAR, R>;
+    best = 8;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+        cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(32);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) best = 16;
+    }
+    cudaGetLastError();
+  }
+  cache[dev] = best;
+  return best > 0 ? best : 0;
+}
+
+template <int EQ, bool CHAR, typename R>
+static cudaError_t cluster_launch(const Step1D& A, int nsteps, int nb, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = nb;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, step1d_cluster_kernel<EQ, CHAR, R>, A, nsteps);
+}
+
 template <int EQ, bool CHAR, typename R, int BW, bool FIELDS>
 static cudaError_t coop_launch(const Step1D& A, int nsteps, int items, cudaStream_t st) {
   auto kern = step1d_coop_kernel<EQ, CHAR, R, BW, FIELDS>;
@@ -130,6 +297,10 @@ template <int EQ, bool CHAR, typename R>
 static cudaError_t steps1d_t(const Step1D& A, int nsteps, cudaStream_t st) {
   const int nx = A.P.nx;
   TileShape ts = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, nx, 1);
+  // a grid that fits one cluster runs resident in it, unless the autotuner chose a layout
+  const int nb = (nx + kClusterW - 1) / kClusterW;
+  if (ts.width == 0 && ts.lanes == 0 && nb <= cluster_max<EQ, CHAR, R>())
+    return cluster_launch<EQ, CHAR, R>(A, nsteps, nb, st);
   if constexpr (EQ == EQ_EULER && CHAR) {
     if (ts.lanes == 4) {
       const int w = ts.width ? ts.width : 128;

@@ -11,8 +11,34 @@
 
 namespace hw {
 
-template <int EQ, bool CHAR, typename R, int BW>
-__device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S, int blk) {
+// Where a 1D item's stage input, base state U^n, V-hat, output and scalars live: device
+// memory through the stage's pointers (the per-stage launches); stage1d_cluster.cuh has the
+// shared-memory counterpart of a solve resident in a thread-block cluster.
+struct Global1D {
+  const KStage& S;
+  int nx;
+  // moment array a (component c = a / 2, moment a % 2) of cell i
+  __device__ __forceinline__ double in(int a, int i) const { return S.Uin[(size_t)a * nx + i]; }
+  __device__ __forceinline__ double un(int a, int i) const { return S.Un[(size_t)a * nx + i]; }
+  __device__ __forceinline__ double vh(int c, int i) const { return S.Vh[(size_t)c * nx + i]; }
+  __device__ __forceinline__ void set_vh(int c, int i, double v) const {
+    S.Vh[(size_t)c * nx + i] = v;
+  }
+  __device__ __forceinline__ void out(int a, int i, double v) const {
+    S.Uout[(size_t)a * nx + i] = v;
+  }
+  __device__ __forceinline__ double dt() const { return *S.dt; }
+  __device__ __forceinline__ double alpha() const { return S.alpha_in[0]; }
+  __device__ __forceinline__ int k() const { return S.k; }
+  __device__ __forceinline__ void nonphysical() const { atomicOr(S.status, kStatusNonphysical); }
+  // the block's maximum output wave speed (called once per item, by thread 0)
+  __device__ __forceinline__ void raise_alpha(double m) const {
+    atomic_max_nonneg(&S.alpha_out[0], m);
+  }
+};
+
+template <int EQ, bool CHAR, typename R, int BW, class IO>
+__device__ __forceinline__ void stage1d_item_io(const KProblem& P, const IO& io, int blk) {
   constexpr int NC = (EQ == EQ_EULER) ? 3 : 1;
   constexpr int NM = 2;
   const int nx = P.nx;
@@ -25,13 +51,14 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
   __shared__ R fhat[NC][BW + 1];             // flux at the left face of thread t's cell
   __shared__ double red[BW / 32];
 
-  // a1: load with boundary conditions
+  // a1: load with boundary conditions (unrolled: the loads of a thread are in flight together)
+#pragma unroll 4
   for (int q = t; q < NC * NM * (BW + 2); q += BW) {
     const int a = q / (BW + 2), col = q % (BW + 2);
     const int c = a / NM, m = a % NM;
     int flip;
     const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
-    double val = S.Uin[(size_t)a * nx + ii];
+    double val = io.in(a, ii);
     if (flip) val *= mirror_sign<EQ, 1>(c, m, 1, 0);
     win[a][col] = from_f64<R>(val);
   }
@@ -98,7 +125,7 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
   }
   __syncthreads();
   // a8: LF flux at the right face of cell i (Eq. 2.4), once per face
-  const R alpha = (R)S.alpha_in[0];
+  const R alpha = (R)io.alpha();
   if (need && t < BW - 1 && i < nx) {
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -111,7 +138,8 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
   // a10-a11: right-hand sides (Eq. 2.3) and the stage combination (Eq. 2.13)
   double wmax = 0.0;
   if (upd) {
-    const double dt = *S.dt;
+    const double dt = io.dt();
+    const int k = io.k();
     const R idx = kconst<R>(P.inv_dx, P.inv_dxf);
     double outv[NC * NM];
 #pragma unroll
@@ -121,25 +149,24 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
       const R vol = R(1.0 / 12.0) * (fp[0][c] + fp[3][c]) + R(5.0 / 12.0) * (fp[1][c] + fp[2][c]);
       const R F2 = (vol - R(0.5) * (fl + fr)) * idx;
       const double own_u = (sizeof(R) == sizeof(double)) ? to_f64(win[c * NM][t + 1])
-                                                          : S.Uin[(size_t)(c * NM) * nx + i];
+                                                          : io.in(c * NM, i);
       const double own_v = to_f64(vh[c]);
-      const size_t q0 = (size_t)(c * NM) * nx + i, q1 = q0 + nx;
       double base_u, base_v;
-      if (S.k == 1) {
+      if (k == 1) {
         base_u = own_u;
         base_v = own_v;
-        S.Vh[(size_t)c * nx + i] = own_v;
+        io.set_vh(c, i, own_v);
       } else {
-        base_u = S.Un[q0];
-        base_v = S.Vh[(size_t)c * nx + i];
+        base_u = io.un(c * NM, i);
+        base_v = io.vh(c, i);
       }
       const double au = fma(dt, to_f64(F1), own_u), av = fma(dt, to_f64(F2), own_v);
       double ou, ov;
-      if (S.k == 1) { ou = au; ov = av; }
-      else if (S.k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
+      if (k == 1) { ou = au; ov = av; }
+      else if (k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
       else { ou = fma(1.0 / 3.0, base_u, 2.0 / 3.0 * au); ov = fma(1.0 / 3.0, base_v, 2.0 / 3.0 * av); }
-      S.Uout[q0] = ou;
-      S.Uout[q1] = ov;
+      io.out(c * NM, i, ou);
+      io.out(c * NM + 1, i, ov);
       outv[c * NM] = ou;
       outv[c * NM + 1] = ov;
     }
@@ -158,7 +185,7 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
       wmax = Phys<EQ, double>::speed(P, 0, ua);
     }
     if (bad) {
-      atomicOr(S.status, kStatusNonphysical);
+      io.nonphysical();
       wmax = 0.0;
     }
   }
@@ -171,9 +198,15 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
     double m = red[0];
 #pragma unroll
     for (int w = 1; w < BW / 32; ++w) m = fmax(m, red[w]);
-    atomic_max_nonneg(&S.alpha_out[0], m);
+    io.raise_alpha(m);
   }
   __syncthreads();  // the block may start another item in the same shared memory
+}
+
+template <int EQ, bool CHAR, typename R, int BW>
+__device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S, int blk) {
+  const Global1D io{S, P.nx};
+  stage1d_item_io<EQ, CHAR, R, BW>(P, io, blk);
 }
 
 // One lane per characteristic field (1D Euler with the characteristic decomposition): the

@@ -334,20 +334,33 @@ def test_engine_steps_through_cells_that_need_the_direct_weights():
     assert rel_err(got, U, U0) <= 10.0 * sens + 1e-12, sens
 
 
-@pytest.mark.parametrize("eq,n", [("euler", 400), ("euler", 4000), ("adv", 200), ("burg", 333)])
-def test_1d_advance_in_one_launch_is_bitwise_the_step_by_step_path(eq, n):
-    """hweno_advance runs 1D solves as whole steps in one cooperative launch (grid barriers
-    between the stages); hweno_step launches the step's kernels one by one.  Both run the
-    same per-cell code, so 25 steps give bitwise the same state, time and step count."""
+@pytest.mark.parametrize("eq,n,bc,prec", [
+    ("euler", 400, None, 0), ("euler", 4000, None, 0), ("adv", 200, None, 0),
+    ("burg", 333, None, 0),
+    # grids resident in one thread-block cluster (30 cells per CTA): one CTA, two, the
+    # portable maximum of 8 and one more, 16 CTAs and one more (the cooperative launch)
+    ("adv", 30, None, 0), ("adv", 31, None, 0), ("burg", 240, None, 0), ("burg", 241, None, 0),
+    ("euler", 200, None, 0), ("euler", 200, (2, 2), 0), ("euler", 200, (1, 2), 1),
+    ("euler", 480, None, 0), ("euler", 481, None, 0), ("adv", 97, None, 1)])
+def test_1d_advance_in_one_launch_is_bitwise_the_step_by_step_path(eq, n, bc, prec):
+    """hweno_advance runs 1D solves as whole steps in one launch: resident in one thread-block
+    cluster (cluster barriers between the stages, the state in the CTAs' shared memory) when
+    the grid fits one, else cooperative (grid barriers); hweno_step launches the step's
+    kernels one by one.  All run the same per-cell code, so 25 steps give bitwise the same
+    state, time and step count (every boundary condition, both precisions)."""
+    prec = H.HWENO_MIXED32 if prec else H.HWENO_FP64
     if eq == "euler":
         w = I.shock_tube_1d(4, n=n)
-        hp = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=n, x0=w.x0, x1=w.x1, bc=w.bc)
+        hp = H.make_problem(dim=1, equation=H.HWENO_EULER, nx=n, x0=w.x0, x1=w.x1,
+                            bc=w.bc if bc is None else bc, precision=prec)
     elif eq == "adv":
         w = I.advection_sine_1d(n)
-        hp = H.make_problem(dim=1, equation=H.HWENO_ADVECTION, nx=n, x0=0.0, x1=2.0, ax=1.0)
+        hp = H.make_problem(dim=1, equation=H.HWENO_ADVECTION, nx=n, x0=0.0, x1=2.0, ax=1.0,
+                            precision=prec)
     else:
         w = I.burgers_sine_1d(n)
-        hp = H.make_problem(dim=1, equation=H.HWENO_BURGERS, nx=n, x0=0.0, x1=2.0)
+        hp = H.make_problem(dim=1, equation=H.HWENO_BURGERS, nx=n, x0=0.0, x1=2.0,
+                            precision=prec)
     eng = H.hweno_create()
     try:
         a = H.hweno_open(eng, hp, w.U0)
@@ -360,4 +373,35 @@ def test_1d_advance_in_one_launch_is_bitwise_the_step_by_step_path(eq, n):
     finally:
         H.hweno_destroy(eng)
     assert ta == tb
+    np.testing.assert_array_equal(ua, ub)
+
+
+def test_1d_cluster_path_stops_at_the_end_time_like_the_cooperative_path(tmp_path):
+    """A solve resident in a cluster reaches t_end inside a launch (the last step clipped)
+    and stops there: the same state, time and step count as the cooperative launch of the
+    same solve (selected through a tuning-table entry)."""
+    import torch
+    w = I.advection_sine_1d(200)
+    hp = H.make_problem(dim=1, equation=H.HWENO_ADVECTION, nx=200, x0=0.0, x1=2.0, ax=1.0)
+    name = torch.cuda.get_device_name(0).replace(" ", "_")
+    eng = H.hweno_create()
+    try:
+        a = H.hweno_open(eng, hp, w.U0)
+        na = H.hweno_advance(eng, a, 0.37)
+        ua, ta = H.hweno_get_state(eng, a, np.empty_like(w.U0))
+        path = str(tmp_path / "t.txt")
+        with open(path, "w") as f:
+            f.write(f"{name} 0 0 0 200 1 0 0 32 1\n")
+        assert H.hweno_tuning_load(path) == 1
+        try:
+            b = H.hweno_open(eng, hp, w.U0)
+            nb = H.hweno_advance(eng, b, 0.37)
+            ub, tb = H.hweno_get_state(eng, b, np.empty_like(w.U0))
+        finally:
+            with open(path, "w") as f:
+                f.write(f"{name} 0 0 0 200 1 0 0 0 0\n")
+            H.hweno_tuning_load(path)
+    finally:
+        H.hweno_destroy(eng)
+    assert ta == tb == 0.37 and na == nb > 0
     np.testing.assert_array_equal(ua, ub)
