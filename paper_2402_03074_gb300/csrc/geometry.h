@@ -67,7 +67,7 @@ inline Geom2D geom2d(int nx, int ny, int bw, int slots, int rows_fixed, int band
 // Rows per work item for the 2D solves of one batched class (bands[s] bands and ny[s] rows
 // each) whose persistent launch has `slots` resident blocks.  The launch runs
 // ceil(items / slots) waves, a partial last wave costing a whole item time, and an item costs
-// its rows plus about 1.5 rows (its two ring rows of the y pass and the four-row window
+// its rows plus about 1.5 rows (its two ring rows of the y pass and the three-row window
 // prologue); the rows minimising waves x (rows + 1.5) give the shortest launch, the smallest
 // such rows (the most items) winning ties.
 inline int batch_rows(const int* bands, const int* ny, int n, int slots) {

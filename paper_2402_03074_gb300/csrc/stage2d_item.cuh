@@ -5,7 +5,7 @@
 // Decomposition: a block owns a band of wout <= BW-2 output columns and a chunk of output
 // rows [j0, j1).  Its threads stand for the columns i0-1 .. i0+wout (the band plus one ring
 // column on each side) and sweep the rows j0-1 .. j1 in order.  At row j every thread
-// reconstructs its cell (i, j) once from a 4-row shared-memory window of the stage input;
+// reconstructs its cell (i, j) once from a 3-row shared-memory window of the stage input;
 // the x-face fluxes of row j are formed once per face through shared memory, the y-face
 // flux between rows j-1 and j is formed by the column's own thread from the top traces it
 // kept from row j-1, and the cell (i, j-1) is then complete: its stage update is written
