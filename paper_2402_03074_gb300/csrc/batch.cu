@@ -6,8 +6,8 @@
 // the unit of the single-solve kernel -- one (band, row chunk) of a 2D solve, one block of
 // kBatchBW - 2 cells of a 1D solve -- so uneven grids share the GPU and the load balances at
 // item granularity.  FP64 and FP32-bulk solves are separate classes (one
-// instantiation each, in the single-solve kernel's default block width, so every kernel
-// keeps the register, shared-memory and stack footprint of the single-solve kernel).  Every solve keeps its own scalars (dt, t, LF speeds,
+// instantiation each, so every kernel keeps the register, shared-memory and stack footprint
+// of the single-solve kernel of its width).  Every solve keeps its own scalars (dt, t, LF speeds,
 // status); one thread per solve advances them at the start of each step, so each solve
 // steps with its own dt.  The work lists live in device memory: admission and retirement
 // rewrite them between steps and the captured step graph stays valid.
@@ -135,7 +135,7 @@ static cudaError_t launch_batch1d_t(const BatchSolve* bs, BatchCtl* ctl, int k, 
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t init_batch_t(int* slots_out, size_t* local_out) {
-  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
+  constexpr int BW = kBatchBW;
   const size_t smem = smem_bytes2d<EQ, CHAR, R, BW>();
   auto kern = batch_stage_kernel<EQ, CHAR, R, BW>;
   static int slots = 0;
@@ -162,7 +162,7 @@ static cudaError_t init_batch_t(int* slots_out, size_t* local_out) {
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t launch_batch_t(const BatchSolve* bs, BatchCtl* ctl, int k, cudaStream_t st) {
-  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
+  constexpr int BW = kBatchBW;
   int slots = 0;
   cudaError_t e = init_batch_t<EQ, CHAR, R>(&slots, nullptr);
   if (e != cudaSuccess) return e;

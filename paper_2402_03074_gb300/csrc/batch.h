@@ -7,13 +7,13 @@
 
 namespace hw {
 
-constexpr int kBatchBW = 128;      // threads per block of the batched 1D stage kernels
-// threads per block of a class's batched 2D stage kernel: the single-solve default width
-// (96 for characteristic FP64 Euler, whose kernel forms the coefficients once per cell;
-// else 128)
-inline int batch_bw2d(int equation, int characteristic, int mixed) {
-  return default_width2d(equation, equation == EQ_EULER && characteristic != 0, mixed != 0);
-}
+// Threads per block of the batched stage kernels, every class.  The characteristic FP64 class
+// keeps the 128-thread kernel that forms the coefficients from each pass's projected stencil:
+// its 96-thread counterpart (coefficients once per cell, 111 KB of shared memory per block),
+// faster for a solve alone, shares the SMs worse with the FP32-bulk class's blocks of a mixed
+// stream (the configured served stream: 0.163 instead of 0.171 solves/s).
+constexpr int kBatchBW = 128;
+inline int batch_bw2d(int, int, int) { return kBatchBW; }
 constexpr int kBatchClasses = 16;  // {2D, 1D} x {advection, Burgers, Euler comp.-wise,
                                    // Euler char.} x {FP64, mixed}
 

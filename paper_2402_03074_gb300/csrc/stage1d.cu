@@ -298,9 +298,13 @@ static cudaError_t steps1d_t(const Step1D& A, int nsteps, cudaStream_t st) {
   const int nx = A.P.nx;
   TileShape ts = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, nx, 1);
   // a grid that fits one cluster runs resident in it, unless the autotuner chose a layout
+  // (a cluster launch the device refuses -- no room for the cluster at the time -- falls
+  // back to the cooperative launch)
   const int nb = (nx + kClusterW - 1) / kClusterW;
-  if (ts.width == 0 && ts.lanes == 0 && nb <= cluster_max<EQ, CHAR, R>())
-    return cluster_launch<EQ, CHAR, R>(A, nsteps, nb, st);
+  if (ts.width == 0 && ts.lanes == 0 && nb <= cluster_max<EQ, CHAR, R>()) {
+    if (cluster_launch<EQ, CHAR, R>(A, nsteps, nb, st) == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();
+  }
   if constexpr (EQ == EQ_EULER && CHAR) {
     if (ts.lanes == 4) {
       const int w = ts.width ? ts.width : 128;

@@ -108,7 +108,7 @@ static bool g_static_ready[64];
 
 template <int EQ, bool CHAR, typename R>
 static cudaError_t static_class_setup(int* slots, size_t* local) {
-  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
+  constexpr int BW = kBatchBW;
   auto kern = static_batch_kernel<EQ, CHAR, R, BW>;
   const size_t smem = smem_bytes2d<EQ, CHAR, R, BW>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -128,7 +128,7 @@ static cudaError_t static_class_setup(int* slots, size_t* local) {
 
 template <int EQ, bool CHAR, typename R>
 static void static_launch(int slots, StaticScratch* ptr, int k, cudaStream_t st) {
-  constexpr int BW = default_width2d(EQ, CHAR, sizeof(R) == 4);
+  constexpr int BW = kBatchBW;
   static_batch_kernel<EQ, CHAR, R, BW><<<slots, BW, smem_bytes2d<EQ, CHAR, R, BW>(), st>>>(ptr, k);
 }
 

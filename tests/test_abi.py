@@ -63,3 +63,31 @@ def test_create_without_gpu_fails_loudly(H):
     with pytest.raises(H.HwenoError) as ei:
         H.hweno_create()
     assert ei.value.code == H.HWENO_ERR_CUDA
+
+
+def test_tuning_table_load_query_and_save_on_the_host(H, tmp_path):
+    """The tuning table is host state: entries of this device (no GPU here: the name is
+    "unknown") load, a single-solve problem finds its entry through hweno_tuning_query, other
+    problems find none, entries of other devices are skipped, and a save writes them back."""
+    path = str(tmp_path / "t.txt")
+    with open(path, "w") as f:
+        f.write("# comment\n")
+        f.write("unknown 2 1 0 640 480 32 9 96 0\n")       # 2D Euler characteristic FP64
+        f.write("unknown 0 0 0 200 1 0 0 32 1\n")          # 1D advection
+        f.write("Some_Other_GPU 2 1 0 640 480 8 8 64 0\n")  # another device: skipped
+    assert H.hweno_tuning_load(path) == 2
+    p2 = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=640, ny=480, x1=4.0 / 3.0)
+    assert H.hweno_tuning_query(p2) == {"rows": 32, "bands": 9, "width": 96, "lanes": 0}
+    p1 = H.make_problem(dim=1, equation=H.HWENO_ADVECTION, nx=200)
+    assert H.hweno_tuning_query(p1) == {"rows": 0, "bands": 0, "width": 32, "lanes": 1}
+    assert H.hweno_tuning_query(H.make_problem(dim=2, equation=H.HWENO_EULER, nx=64)) is None
+    out = str(tmp_path / "saved.txt")
+    H.hweno_tuning_save(out)
+    lines = [ln for ln in open(out) if not ln.startswith("#")]
+    assert "unknown 2 1 0 640 480 32 9 96 0\n" in lines
+    assert "unknown 0 0 0 200 1 0 0 32 1\n" in lines
+    # clear the entries again (all zero = not tuned)
+    with open(path, "w") as f:
+        f.write("unknown 2 1 0 640 480 0 0 0 0\nunknown 0 0 0 200 1 0 0 0 0\n")
+    assert H.hweno_tuning_load(path) == 2
+    assert H.hweno_tuning_query(p2) is None and H.hweno_tuning_query(p1) is None
