@@ -253,7 +253,8 @@ int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* mome
 int hweno_tuning_save(const char* path);
 int hweno_tuning_load(const char* path);
 /* The tuning-table entry a single-solve launch of problem p would use: *rows, *bands (2D tile
-   shape; 0 = the default, -1 = the default chosen by the autotuner), *width (block width: 2D
+   shape; 0 = the default, -1 = the default chosen by the autotuner; rows < -1: the bands'
+   rows swept in segments of -rows band-rows, one per block), *width (block width: 2D
    128, 96 or 64, 1D 128, 64 or 32; 0 = the default) and *lanes (1D threads per cell).  Returns 1
    when the table has an entry for p, 0 when not (all outputs 0), HWENO_ERR_ARG for a NULL or
    malformed p.  Output pointers may be NULL. */

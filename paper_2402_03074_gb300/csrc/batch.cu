@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
     S.status = &B.sc->status;
     S.active = &B.sc->active;
     S.k = k;
-    stage2d_item<EQ, CHAR, R, BW>(B.P, S, band, chunk, B.rows, B.wout, smem, red);
+    const int j0 = chunk * B.rows;
+    stage2d_item<EQ, CHAR, R, BW>(B.P, S, band, j0, min(B.P.ny, j0 + B.rows), B.wout, smem, red);
   }
 }
 

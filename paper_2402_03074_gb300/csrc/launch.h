@@ -57,9 +57,10 @@ __device__ __forceinline__ void dt_update(DevScal* s, double inv_dx, double inv_
   s->active = 1;
 }
 
-// Tile shape of the 2D single-solve launch: rows per chunk (tile height) and number of bands
-// (tile width = ceil(nx / bands) output columns); 0 = the default for that dimension (one
-// wave of blocks over the resident slots; the widest bands).
+// Tile shape of the 2D single-solve launch: rows per chunk (tile height; < -1: segments of
+// -rows band-rows, geometry.h) and number of bands (tile width = ceil(nx / bands) output
+// columns); 0 = the default for that dimension (one wave of blocks over the resident slots, in
+// chunks or segments; the widest bands).
 struct TileShape {
   int rows = 0;
   int bands = 0;

@@ -6,14 +6,30 @@
 
 namespace hw {
 
-// single-solve kernel: one block per (band, chunk)
+// single-solve kernel (geometry.h): chunks (seg = 0), one block per (band, row chunk); or
+// segments, block b sweeping the band-rows [b seg, (b + 1) seg) of the `bands` bands taken one
+// after another, in one piece per band it touches
 template <int EQ, bool CHAR, typename R, int BW>
 __global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
-    stage2d_kernel(KProblem P, KStage S, int rows, int wout) {
+    stage2d_kernel(KProblem P, KStage S, int rows, int wout, int seg, int bands) {
   if (S.active && *S.active == 0) return;
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];
-  stage2d_item<EQ, CHAR, R, BW>(P, S, blockIdx.x, blockIdx.y, rows, wout, smem, red);
+  const int ny = P.ny;
+  if (seg == 0) {
+    const int j0 = blockIdx.y * rows;
+    stage2d_item<EQ, CHAR, R, BW>(P, S, blockIdx.x, j0, min(ny, j0 + rows), wout, smem, red);
+    return;
+  }
+  long long q = (long long)blockIdx.x * seg;
+  const long long qend = min(q + seg, (long long)bands * ny);
+#pragma unroll 1
+  while (q < qend) {  // uniform over the block
+    const int band = (int)(q / ny), j0 = (int)(q - (long long)band * ny);
+    const int j1 = (int)min((long long)ny, (long long)j0 + (qend - q));
+    stage2d_item<EQ, CHAR, R, BW>(P, S, band, j0, j1, wout, smem, red);
+    q += j1 - j0;
+  }
 }
 
 static thread_local TileShape g_force_shape;
@@ -50,12 +66,13 @@ static cudaError_t launch2d_w(const KProblem& P, const KStage& S, TileShape t, c
   int slots = 0;
   cudaError_t e = init2d_t<EQ, CHAR, R, BW>(&slots, nullptr);
   if (e != cudaSuccess) return e;
-  // bands of equal width and row chunks filling the resident block slots once, unless the
-  // tuning table (or the autotuner) fixes the tile shape (geometry.h)
-  const Geom2D g = geom2d(P.nx, P.ny, BW, slots, t.rows > 0 ? t.rows : 0,
+  // bands of equal width, swept in row chunks or segments filling the resident block slots
+  // once, unless the tuning table (or the autotuner) fixes the tile shape (geometry.h)
+  const Geom2D g = geom2d(P.nx, P.ny, BW, slots, (t.rows > 0 || t.rows < -1) ? t.rows : 0,
                           t.bands > 0 ? t.bands : 0, sizeof(R) == sizeof(double));
-  dim3 grid(g.bands, g.chunks);
-  stage2d_kernel<EQ, CHAR, R, BW><<<grid, BW, smem_bytes2d<EQ, CHAR, R, BW>(), st>>>(P, S, g.rows, g.wout);
+  const dim3 grid = g.seg > 0 ? dim3(g.blocks) : dim3(g.bands, g.chunks);
+  stage2d_kernel<EQ, CHAR, R, BW><<<grid, BW, smem_bytes2d<EQ, CHAR, R, BW>(), st>>>(
+      P, S, g.rows, g.wout, g.seg, g.bands);
   return cudaGetLastError();
 }
 

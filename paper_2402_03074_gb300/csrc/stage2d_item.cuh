@@ -53,8 +53,8 @@ __device__ __forceinline__ void volume_sum(const KProblem& P, int dir, const R (
   }
 }
 
-// One work item: band `band` (output columns band*wout .. +wout-1) and row chunk `chunk`
-// (output rows chunk*rows .. +rows-1) of one stage of one solve, processed by a whole block.
+// One work item: band `band` (output columns band*wout .. +wout-1) and the output rows
+// [j0, j1) of one stage of one solve, processed by a whole block.
 // smem: dynamic shared memory of smem_bytes2d<EQ, CHAR, R, BW>(); red: 2*(BW/32) doubles.
 // The row window holds the stage input in the bulk precision R (converted once per value
 // when a row is loaded); the FP64 update reads the cell's own averages from global memory
@@ -83,7 +83,7 @@ constexpr size_t smem_bytes2d() {
 
 template <int EQ, bool CHAR, typename R, int BW>
 __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S, int band,
-                                             int chunk, int rows, int wout, double* smem,
+                                             int j0, int j1, int wout, double* smem,
                                              double (*red)[BW / 32]) {
   constexpr int NC = (EQ == EQ_EULER) ? 4 : 1;
   constexpr int NM = 3;
@@ -112,8 +112,6 @@ __device__ __forceinline__ void stage2d_item(const KProblem& P, const KStage& S,
   const int t = threadIdx.x;
   const int i0 = band * wout;   // wout <= BW - 2 output columns per band
   const int i = i0 - 1 + t;
-  const int j0 = chunk * rows;
-  const int j1 = min(ny, j0 + rows);
   const bool need = (t <= wout + 1) && (i <= nx);
   const bool outc = (t >= 1 && t <= wout && i < nx);
   const R a1 = (R)S.alpha_in[0], a2 = (R)S.alpha_in[1];

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
     S.status = B.status;
     S.active = nullptr;
     S.k = k;
-    stage2d_item<EQ, CHAR, R, BW>(B.P, S, local % B.bands, local / B.bands, B.rows, B.wout,
+    const int j0 = (local / B.bands) * B.rows;
+    stage2d_item<EQ, CHAR, R, BW>(B.P, S, local % B.bands, j0, min(B.P.ny, j0 + B.rows), B.wout,
                                   smem, red);
   }
 }

@@ -25,7 +25,7 @@ int main() {
       int nx, ny, bw, slots, rf, bf, lane;
       if (std::scanf("%d %d %d %d %d %d %d", &nx, &ny, &bw, &slots, &rf, &bf, &lane) != 7) return 2;
       const hw::Geom2D g = hw::geom2d(nx, ny, bw, slots, rf, bf, lane != 0);
-      std::printf("%d %d %d %d\n", g.bands, g.wout, g.chunks, g.rows);
+      std::printf("%d %d %d %d %d %d\n", g.bands, g.wout, g.chunks, g.rows, g.seg, g.blocks);
     } else if (op == 'R') {
       int slots, n;
       if (std::scanf("%d %d", &slots, &n) != 2) return 2;
@@ -79,14 +79,24 @@ def test_single_solve_covers_the_grid_in_one_wave(geo):
     cases += [(1, 1, 128, 304, 0, 0, 1), (2, 3, 128, 304, 0, 0, 0), (126, 1, 128, 304, 0, 0, 0),
               (127, 2, 128, 304, 0, 0, 1), (4096, 4096, 128, 304, 0, 0, 1)]
     out = geo(["G " + " ".join(map(str, c)) for c in cases])
-    for (nx, ny, bw, slots, _, _, lane), (bands, wout, chunks, rows) in zip(cases, out):
+    nseg = 0
+    for (nx, ny, bw, slots, _, _, lane), (bands, wout, chunks, rows, seg, blocks) in zip(cases, out):
         assert 1 <= wout <= bw - 2
         assert bands * wout >= nx and (bands - 1) * wout < nx    # every column, no empty band
         assert rows * chunks >= ny and (chunks - 1) * rows < ny  # every row, no empty chunk
+        if seg == 0:
+            assert blocks == bands * chunks
+        else:                                                     # every band-row, no empty block
+            nseg += 1
+            assert blocks * seg >= bands * ny and (blocks - 1) * seg < bands * ny
+            # chosen only where it is 2 % cheaper: pieces of seg rows + 1.5 against chunks
+            pieces = 1 + math.ceil((seg - 1) / ny)
+            assert seg + 1.5 * pieces < 0.98 * (rows + 1.5)
         if bands <= slots:
-            assert bands * chunks <= slots                       # one wave of blocks
+            assert blocks <= slots                               # one wave of blocks
         if not lane:
             assert bands <= math.ceil(nx / (bw - 2)) and wout >= min(nx, bw - 2) // 2
+    assert nseg > 0
 
 
 def test_lane_aware_bands(geo):
@@ -97,8 +107,10 @@ def test_lane_aware_bands(geo):
                "G 1024 1024 128 304 0 0 1", "G 1024 1024 128 304 0 0 0"])
     assert out[0][:2] == [22, 94] and out[1][:2] == [17, 121]
     assert out[2][:2] == [11, 94] and out[3][:2] == [9, 114]
-    # one wave: 22 x 13 = 286 and 11 x 27 = 297 blocks on 304 slots
-    assert out[0][0] * out[0][2] == 286 and out[2][0] * out[2][2] == 297
+    # one wave on 304 slots: 22 bands of 2048 rows in 303 segments of 149 band-rows (22 x 13 =
+    # 286 chunks of 158 rows would leave 18 slots empty); 11 x 27 = 297 chunks of 38 rows
+    assert out[0][4:] == [149, 303] and out[0][0] * out[0][2] == 286
+    assert out[2][4:] == [0, 297] and out[2][0] * out[2][2] == 297
     # the lane-aware choice is taken only when it saves lanes
     rng = np.random.default_rng(3)
     nxs = [int(v) for v in rng.integers(1, 6000, size=200)]
@@ -116,11 +128,15 @@ def test_fixed_tile_shapes(geo):
     out = geo(["G 2048 2048 128 304 32 0 1",    # rows fixed
                "G 2048 2048 128 304 0 4 1",     # too few bands: raised to the 126-column bound
                "G 2048 2048 128 304 0 40 0",    # more bands than the default
-               "G 100 50 128 304 500 0 0"])     # rows above ny: one chunk
-    assert out[0][3] == 32 and out[0][2] == 64
+               "G 100 50 128 304 500 0 0",      # rows above ny: one chunk
+               "G 300 37 96 304 -7 0 1",        # segments of 7 band-rows
+               "G 300 37 96 304 -100000 0 1"])  # a segment longer than all bands: one block
+    assert out[0][3] == 32 and out[0][2] == 64 and out[0][4] == 0
     assert out[1][0] == 17 and out[1][1] == 121
     assert out[2][0] == 40 and out[2][1] == 52
-    assert out[3][2:] == [1, 50]
+    assert out[3][2:4] == [1, 50] and out[3][4] == 0
+    assert out[4][0] == 5 and out[4][4:] == [7, math.ceil(5 * 37 / 7)]   # 5 bands of 60
+    assert out[5][4:] == [5 * 37, 1]
 
 
 def test_batched_rows_minimise_the_waves(geo):

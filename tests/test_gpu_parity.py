@@ -33,6 +33,33 @@ def _inputs(op, seed):
     return Uin, Un, Vh
 
 
+def physical_seed(op, k, seed, sens_max=1e-13):
+    """The first seed from `seed` (then steps of 1000) whose random stage-k input the oracle
+    maps to a physical output that is well conditioned: a random state can drive a cell's
+    pressure negative (outside the scheme's domain), or put a cell where its sensitivity to a
+    1-ulp change of the input (measured: two sign-random 1-ulp perturbations of U_in) exceeds
+    `sens_max` -- 2e-11 and 3.9e-12 in two such cases -- where no implementation can meet the
+    1e-12 bar."""
+    for s in range(seed, seed + 20000, 1000):
+        Uin, Un, Vh = _inputs(op, s)
+        Un_k = Uin if k == 1 else Un
+        Vh_k = Vh if k > 1 else None
+        alpha = O.alpha(op, Uin)
+        dt = 0.3 / (alpha[0] / ((op.x1 - op.x0) / op.nx) + (alpha[1] / ((op.y1 - op.y0) / op.ny) if op.dim == 2 else 0.0))
+        ref, _, st = O.stage(op, k, Uin, Un_k, Vh_k, alpha, dt)
+        if st != 0:
+            continue
+        sens = 0.0
+        for r in range(2):
+            flips = np.random.default_rng(7 + r).choice([-1.0, 0.0, 1.0], size=Uin.shape)
+            U2 = Uin * (1.0 + 2.0 ** -52 * flips)
+            out2 = O.stage(op, k, U2, U2 if k == 1 else Un, Vh_k, alpha, dt)[0]
+            sens = max(sens, rel_err(out2, ref, Uin))
+        if sens <= sens_max:
+            return s
+    raise AssertionError("no physical, well-conditioned seed")
+
+
 def _check_stage(op, hp, k, seed, tol=TOL):
     Uin, Un, Vh = _inputs(op, seed)
     if k == 1:

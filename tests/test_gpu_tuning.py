@@ -234,22 +234,10 @@ def test_block_widths_2d_match_oracle(tmp_path, width):
     stage (the 96-thread kernel projects the conserved coefficients formed once per cell, the
     others form the coefficients from the projected stencil), on grids of one band less one
     column, one band, one band plus one column and several bands with a ragged tail, every
-    boundary condition.  Each case takes the first seed (13 k + nx, then steps of 1000) whose
-    stage output the oracle finds physical: a random state can drive a cell's pressure negative,
-    where the output lies outside the scheme's domain and its sensitivity to a 1-ulp change of
-    the input (2e-11 in one such case) exceeds the tolerance."""
+    boundary condition.  Each case takes the first seed from 13 k + nx whose stage the oracle
+    finds physical and well conditioned (physical_seed)."""
     from gpu_helpers import problems
-    from test_gpu_parity import _check_stage, _inputs
-    import oracle as O
-
-    def physical_seed(op, k, seed):
-        for s in range(seed, seed + 10000, 1000):
-            Uin, Un, Vh = _inputs(op, s)
-            alpha = O.alpha(op, Uin)
-            dt = 0.3 / (alpha[0] / ((op.x1 - op.x0) / op.nx) + alpha[1] / ((op.y1 - op.y0) / op.ny))
-            if O.stage(op, k, Uin, Uin if k == 1 else Un, Vh if k > 1 else None, alpha, dt)[2] == 0:
-                return s
-        raise AssertionError("no physical seed")
+    from test_gpu_parity import _check_stage, physical_seed
     wb = width - 2
     sizes = [(wb - 1, 5), (wb, 7), (wb + 1, 3), (3 * wb + 5, 11)]
     path = _tuning_file_2d(tmp_path, [(2, 1, 0, nx, ny, width) for nx, ny in sizes])
@@ -283,3 +271,38 @@ def test_block_widths_2d_same_bits_where_the_arithmetic_is_the_same(tmp_path):
         np.testing.assert_array_equal(outs[64], outs[128])
         if not (ch == 1 and mixed == 0):   # the 96-thread FP64 characteristic kernel differs
             np.testing.assert_array_equal(outs[96], outs[128])
+
+
+@pytest.mark.parametrize("seg", [7, 23, 37, 41, 150])
+def test_segment_layout_matches_oracle_and_the_chunk_layout(tmp_path, seg):
+    """The segment layout (tuning entry rows = -seg): the bands' rows taken one after another
+    and cut into segments of `seg` band-rows, one per block, a segment that crosses the end of
+    a band swept in two or more pieces (seg = 150 > the 4 x 37 band-rows: one block sweeps all
+    four bands).  Characteristic FP64 2D Euler on 200 x 37 cells (4 bands of 50 columns):
+    every stage against the oracle at 1e-12 for every boundary condition, and bitwise the
+    default chunk layout (the decomposition changes no cell's arithmetic).  Seeds whose stage
+    the oracle finds physical and well conditioned (physical_seed)."""
+    import torch
+    from gpu_helpers import gpu_problems_stage, problems
+    from test_gpu_parity import _check_stage, physical_seed
+    name = torch.cuda.get_device_name(0).replace(" ", "_")
+    nx, ny = 200, 37
+    ref = {ch: gpu_problems_stage(nx, ny, ch, 0, seed=5) for ch in (1, 0)}
+    path = str(tmp_path / "seg.txt")
+    with open(path, "w") as f:
+        f.write(f"{name} 2 1 0 {nx} {ny} {-seg} 0 0 0\n{name} 2 0 0 {nx} {ny} {-seg} 0 0 0\n")
+    assert H.hweno_tuning_load(path) == 2
+    try:
+        q = H.hweno_tuning_query(H.make_problem(dim=2, equation=H.HWENO_EULER, nx=nx, ny=ny,
+                                                x1=1.0, y1=ny / nx))
+        assert q["rows"] == -seg
+        for ch in (1, 0):
+            np.testing.assert_array_equal(gpu_problems_stage(nx, ny, ch, 0, seed=5), ref[ch])
+        for bc in (0, 1, 2):
+            op, hp = problems(2, "euler", nx, ny, bc=bc, characteristic=1)
+            for k in (1, 2, 3):
+                _check_stage(op, hp, k, seed=physical_seed(op, k, 29 * k + seg))
+    finally:
+        with open(path, "w") as f:
+            f.write(f"{name} 2 1 0 {nx} {ny} 0 0 0 0\n{name} 2 0 0 {nx} {ny} 0 0 0 0\n")
+        H.hweno_tuning_load(path)
