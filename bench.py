@@ -45,21 +45,22 @@ FP64_PEAK_TFLOPS_FALLBACK = 1.19
 FP32_PEAK_TFLOPS_FALLBACK = 74.2
 # FP64 arithmetic the fused 2D Euler characteristic kernel executes per cell-stage, from the
 # ncu thread-instruction counts of one 2048^2 launch in its default geometry (96-thread
-# blocks, 22 bands of 94 columns, 13 row chunks; profiles/stage2d_euler_2048_instruction_counts.md)
-# per updated cell less the 2.8 % of redundant ring-cell reconstruction: operations (DFMA +
-# DMUL + DADD) 3445 -> 3351.  The FP64 pipe executes one such operation per lane per clock,
-# so its operation rate is half the FMA flop rate.
+# blocks, 22 bands of 94 columns in 303 segments of 149 band-rows;
+# profiles/stage2d_euler_2048_instruction_counts.md) per updated cell less the 2.9 % of
+# redundant ring-cell reconstruction: operations (DFMA + DMUL + DADD) 3447 -> 3351.  The FP64
+# pipe executes one such operation per lane per clock, so its operation rate is half the FMA
+# flop rate.
 FP64_OPS_PER_CELL_STAGE = 3351.0
 # DRAM bytes read + written by the same launch (ncu)
-FP64_STAGE_DRAM_BYTES = 422.2e6 + 708.6e6
+FP64_STAGE_DRAM_BYTES = 524.4e6 + 725.1e6
 # FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.832
+FP64_PIPE_UTIL_NCU = 0.839
 # FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (928 per
 # reconstructed cell less 2.9 % ring redundancy at three blocks per SM), FP32 flops, and the
 # launch's DRAM bytes
 FP32BULK_FP64_OPS_PER_CELL_STAGE = 902.0
 FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 3971.0
-FP32BULK_STAGE_DRAM_BYTES = 463.1e6 + 1052.1e6
+FP32BULK_STAGE_DRAM_BYTES = 468.2e6 + 1088.6e6
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
