@@ -124,14 +124,39 @@ __global__ void __launch_bounds__(BW) step1d_coop_kernel(Step1D A, int nsteps, i
 // results are bitwise those of the per-stage launches.
 constexpr int kClusterW = 30;  // cells per one-warp CTA
 
-template <int NA, int W>
+// The sources of one thread's window entries, the same every stage: for window slot s (entry
+// t + 32 s of the item's [NA][W + 4] window, flat index widx[s], -1 if none) the owner CTA's
+// address of the moment in each of the three stage buffers, and whether a mirror boundary
+// flips its sign.
+template <int SL>
+struct ClusterWin {
+  const double* src[3][SL];
+  int widx[SL];
+  bool neg[SL];
+};
+
+template <int NA, int W, int SL, typename R>
 struct Cluster1D {
+  static constexpr bool kTabulated = true;
   double (*st)[NA][W];   // this CTA's [3] stage buffers (U^n, U^(1), U^(2)) of its cells
   double (*vhs)[W];      // this CTA's V-hat of its cells
   double* amax;          // this CTA's maximum output speed of the stage
   unsigned* bad;         // this CTA's non-physical flag of the stage
+  const ClusterWin<SL>* tab;
   int kin, kout, kk, i0;
   double dtv, alphav;
+  __device__ __forceinline__ void fill(R* win) const {
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      const int w = tab->widx[s];
+      if (w >= 0) {
+        // (selects, not an index: the table stays in registers)
+        const double* p = kin == 0 ? tab->src[0][s] : (kin == 1 ? tab->src[1][s] : tab->src[2][s]);
+        const double v = *p;
+        win[w] = from_f64<R>(tab->neg[s] ? -v : v);
+      }
+    }
+  }
   __device__ __forceinline__ double in(int a, int i) const {
     const int owner = i / W;
     cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
@@ -178,6 +203,7 @@ __device__ __forceinline__ void cluster_reduce(DevScal& sc, double (*amax)[1], u
 template <int EQ, bool CHAR, typename R>
 __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps) {
   constexpr int BW = 32, W = kClusterW, NC = (EQ == EQ_EULER) ? 3 : 1, NA = NC * 2;
+  constexpr int SL = (NA * (BW + 2) + BW - 1) / BW;  // window entries per thread
   static_assert(W == BW - 2, "one thread per reconstructed cell");
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double st[3][NA][W];
@@ -198,6 +224,24 @@ __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps
       bad[k][0] = 0u;
     }
   }
+  // the window's sources (the item's window: cells i0 - 2 .. i0 + BW - 1, boundary-mapped)
+  ClusterWin<SL> tab;
+#pragma unroll
+  for (int s = 0; s < SL; ++s) {
+    const int q = t + s * BW;
+    tab.widx[s] = -1;
+    tab.neg[s] = false;
+    for (int b = 0; b < 3; ++b) tab.src[b][s] = nullptr;
+    if (q < NA * (BW + 2)) {
+      const int a = q / (BW + 2), col = q - a * (BW + 2);
+      int flip;
+      const int ii = bc_map(i0 - 2 + col, nx, A.P.bc[0], A.P.bc[1], flip);
+      const int owner = ii / W;
+      for (int b = 0; b < 3; ++b) tab.src[b][s] = cl.map_shared_rank(&st[b][a][ii - owner * W], owner);
+      tab.widx[s] = q;
+      tab.neg[s] = flip && mirror_sign<EQ, 1>(a / 2, a % 2, 1, 0) < 0.0;
+    }
+  }
 #pragma unroll 1
   for (int s = 0;; ++s) {
     cl.sync();  // stage 3 of the previous step is complete in every CTA
@@ -212,8 +256,8 @@ __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps
         cluster_reduce(scl, amax, bad, k - 1, nb);
         __syncthreads();
       }
-      Cluster1D<NA, W> io{st, vhs, &amax[k][0], &bad[k][0], k - 1, k % 3, k, i0,
-                          scl.dt, scl.alpha[k - 1][0]};
+      Cluster1D<NA, W, SL, R> io{st, vhs, &amax[k][0], &bad[k][0], &tab, k - 1, k % 3, k, i0,
+                                 scl.dt, scl.alpha[k - 1][0]};
       if (t == 0) bad[k][0] = 0u;
       stage1d_item_io<EQ, CHAR, R, BW>(A.P, io, rank);
     }

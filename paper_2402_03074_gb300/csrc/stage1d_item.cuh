@@ -15,6 +15,7 @@ namespace hw {
 // memory through the stage's pointers (the per-stage launches); stage1d_cluster.cuh has the
 // shared-memory counterpart of a solve resident in a thread-block cluster.
 struct Global1D {
+  static constexpr bool kTabulated = false;  // the window is filled by the generic loop
   const KStage& S;
   int nx;
   // moment array a (component c = a / 2, moment a % 2) of cell i
@@ -51,16 +52,21 @@ __device__ __forceinline__ void stage1d_item_io(const KProblem& P, const IO& io,
   __shared__ R fhat[NC][BW + 1];             // flux at the left face of thread t's cell
   __shared__ double red[BW / 32];
 
-  // a1: load with boundary conditions (unrolled: the loads of a thread are in flight together)
+  // a1: load with boundary conditions (unrolled: the loads of a thread are in flight together);
+  // an I/O that tabulated the window's sources once (the same cells every stage) fills it
+  if constexpr (IO::kTabulated) {
+    io.fill(&win[0][0]);
+  } else {
 #pragma unroll 4
-  for (int q = t; q < NC * NM * (BW + 2); q += BW) {
-    const int a = q / (BW + 2), col = q % (BW + 2);
-    const int c = a / NM, m = a % NM;
-    int flip;
-    const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
-    double val = io.in(a, ii);
-    if (flip) val *= mirror_sign<EQ, 1>(c, m, 1, 0);
-    win[a][col] = from_f64<R>(val);
+    for (int q = t; q < NC * NM * (BW + 2); q += BW) {
+      const int a = q / (BW + 2), col = q % (BW + 2);
+      const int c = a / NM, m = a % NM;
+      int flip;
+      const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
+      double val = io.in(a, ii);
+      if (flip) val *= mirror_sign<EQ, 1>(c, m, 1, 0);
+      win[a][col] = from_f64<R>(val);
+    }
   }
   __syncthreads();
 
