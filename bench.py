@@ -748,8 +748,9 @@ def run_paper_tables(args):
          lambda t: I.euler_density_wave_exact_1d(n, t), 1.34e01),
         ("Table 3.4, 2D Burgers", I.burgers_sine_2d(n), H.HWENO_BURGERS,
          lambda t: I.burgers_exact_2d(n, t), 3.69e02),
-        ("Table 3.6, 2D Euler", I.euler_density_wave_2d(n), H.HWENO_EULER,
-         lambda t: I.euler_density_wave_exact_2d(n, t), 2.14e05),
+        # the wavenumber whose errors Table 3.6 prints (sin(pi (x + y) / 2); R20)
+        ("Table 3.6, 2D Euler", I.euler_density_wave_2d(n, k=0.5), H.HWENO_EULER,
+         lambda t: I.euler_density_wave_exact_2d(n, t, k=0.5), 2.14e05),
     ]
     eng = H.hweno_create()
     for name, w, eq, exact, paper_s in cases:
@@ -771,11 +772,12 @@ def run_paper_tables(args):
 
 def run_dt_sweep(args):
     """Time-step dependence of the paper's 2D accuracy examples (Tables 3.4-3.6), FP64: the
-    error against the exact solution of Example 3.3 (2D Burgers, T = 0.5/pi) at 40^2, 80^2,
-    120^2 and Example 3.4 (2D Euler density wave, T = 2) at 40^2, 80^2, for dt = c dx with
-    c in {0.1, 0.02, 0.005} and for the CFL 0.6 rule, with the scale-invariant weights (Eq.
-    2.22) and the linear weights; for Euler also the original weights and the component-wise
-    reconstruction.  One JSON line per run, beside the printed values."""
+    error against the exact solution of Example 3.3 (2D Burgers, T = 0.5/pi) and Example 3.4
+    (2D Euler density wave, T = 2, at the printed wavenumber and at half of it) at 40^2,
+    80^2, 120^2, for dt = c dx with c in {0.1, 0.02, 0.005} and for the CFL 0.6 rule, with the
+    scale-invariant weights (Eq. 2.22) and the linear weights; for Euler at the printed
+    wavenumber also the original weights and the component-wise reconstruction.  One JSON line
+    per run, beside the printed values."""
     from paper_2402_03074_gb300 import build as B
     B.build()
     from paper_2402_03074_gb300 import _binding as H
@@ -790,9 +792,14 @@ def run_dt_sweep(args):
     cases = [("Table 3.4, 2D Burgers", H.HWENO_BURGERS, n, I.burgers_sine_2d(n),
               lambda n, t: I.burgers_exact_2d(n, t), "table_3_4_burgers_2d",
               ("scale-invariant", "linear")) for n in (40, 80, 120)]
-    cases += [("Table 3.6, 2D Euler", H.HWENO_EULER, n, I.euler_density_wave_2d(n),
-               lambda n, t: I.euler_density_wave_exact_2d(n, t), "table_3_6_euler_2d",
-               tuple(variants)) for n in (40, 80)]
+    # Example 3.4 at the printed wavenumber sin(pi (x + y)) and at sin(pi (x + y) / 2), whose
+    # errors Table 3.6 prints (R20)
+    for kk in (1.0, 0.5):
+        cases += [(f"Table 3.6, 2D Euler, k = {kk}", H.HWENO_EULER, n,
+                   I.euler_density_wave_2d(n, k=kk),
+                   lambda n, t, kk=kk: I.euler_density_wave_exact_2d(n, t, k=kk),
+                   "table_3_6_euler_2d", tuple(variants) if kk == 1.0 else
+                   ("scale-invariant", "linear")) for n in (40, 80, 120)]
     for name, eq, n, w, exact, key, names in cases:
         ex = exact(n, w.t_end)
         printed = tables[key].get(str(n))

@@ -303,6 +303,29 @@ def test_2d_burgers_matches_table_3_4_and_3_5(n, tol_l1, tol_linf):
         assert ev.max() == pytest.approx(gv["linf"], rel=0.1)
 
 
+def test_2d_euler_table_3_6_is_the_half_wavenumber():
+    """Example 3.4 (2D Euler density wave, T = 2) with the scale-invariant weights and
+    dt = 0.02 dx, the reading that reproduces Tables 3.4/3.5: at the wavenumber of Example
+    3.3, sin(pi (x + y) / 2), the printed Table 3.6 errors are reproduced at 40^2 (L1 and Linf
+    within 0.75-1.25 of them); at the printed sin(pi (x + y)) the errors are 30x and more
+    above the table (the fifth-order error of a twice as fast-varying wave, 2^5 = 32x, before
+    the weights' response)."""
+    import os
+    g = _golden()["table_3_6_euler_2d"]["40"]
+    n = 40
+    P = O.Problem(dim=2, eq=O.EULER, nx=n, ny=n, x0=0.0, x1=4.0, y0=0.0, y1=4.0)
+    thr = os.cpu_count() or 1
+    errs = {}
+    for k in (0.5, 1.0):
+        w = I.euler_density_wave_2d(n, k=k)
+        U, t, ns, st = O.run(P, w.U0, 0.0, 2.0, dt_fixed=0.02 * 4.0 / n, threads=thr)
+        assert st == 0 and t == 2.0 and ns == 1000
+        e = np.abs(U[0, 0] - I.euler_density_wave_exact_2d(n, 2.0, k=k)[0, 0])
+        errs[k] = (e.mean(), e.max())
+    assert 0.75 < errs[0.5][0] / g["l1"] < 1.25 and 0.75 < errs[0.5][1] / g["linf"] < 1.25
+    assert errs[1.0][0] > 30.0 * g["l1"] and errs[1.0][1] > 30.0 * g["linf"]
+
+
 def _run_example(w):
     P = O.Problem(dim=1, eq=O.EULER, nx=w.nx, x0=w.x0, x1=w.x1, bc=w.bc)
     U, t, ns, st = O.run(P, w.U0, 0.0, w.t_end)
