@@ -43,6 +43,9 @@ __global__ void __launch_bounds__(BW) stage1d_fields_kernel(KProblem P, KStage S
   stage1d_fields_item<R, BW>(P, S, blockIdx.x);
 }
 
+template <int EQ, bool CHAR, typename R>
+static bool short_fields1d(int nx);
+
 // blocks of BW threads, BW - 2 cells each (one thread per cell), or BW / 4 - 2 cells each
 // (one lane per characteristic field)
 template <int EQ, bool CHAR, typename R>
@@ -50,6 +53,10 @@ static cudaError_t launch1d_t(const KProblem& P, const KStage& S, cudaStream_t s
   TileShape ts;
   if (g_force1d.width || g_force1d.lanes) ts = g_force1d;
   else ts = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, P.nx, 1);
+  if (ts.width == 0 && ts.lanes == 0 && short_fields1d<EQ, CHAR, R>(P.nx)) {
+    ts.width = 128;
+    ts.lanes = 4;
+  }
   if constexpr (EQ == EQ_EULER && CHAR) {
     if (ts.lanes == 4) {
       const int w = ts.width ? ts.width : 128;
@@ -200,11 +207,20 @@ __device__ __forceinline__ void cluster_reduce(DevScal& sc, double (*amax)[1], u
   }
 }
 
-template <int EQ, bool CHAR, typename R>
-__global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps) {
-  constexpr int BW = 32, W = kClusterW, NC = (EQ == EQ_EULER) ? 3 : 1, NA = NC * 2;
-  constexpr int SL = (NA * (BW + 2) + BW - 1) / BW;  // window entries per thread
-  static_assert(W == BW - 2, "one thread per reconstructed cell");
+// CTA width of the cluster kernel: one warp (one thread per cell), or 128 threads for one
+// lane per characteristic field (32 cell slots, 1D Euler with the characteristic
+// decomposition); either way a CTA owns kClusterW cells and its item window has
+// kClusterW + 4 columns.
+template <bool FIELDS>
+constexpr int kClusterBW = FIELDS ? 128 : 32;
+
+template <int EQ, bool CHAR, typename R, bool FIELDS>
+__global__ void __launch_bounds__(kClusterBW<FIELDS>) step1d_cluster_kernel(Step1D A,
+                                                                          int nsteps) {
+  constexpr int BW = kClusterBW<FIELDS>, W = kClusterW, NC = (EQ == EQ_EULER) ? 3 : 1;
+  constexpr int NA = NC * 2, WC = W + 4;
+  constexpr int SL = (NA * WC + BW - 1) / BW;  // window entries per thread
+  static_assert(FIELDS ? (W == BW / 4 - 2) : (W == BW - 2), "a CTA owns its item's cells");
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double st[3][NA][W];
   __shared__ double vhs[NC][W];
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps
       bad[k][0] = 0u;
     }
   }
-  // the window's sources (the item's window: cells i0 - 2 .. i0 + BW - 1, boundary-mapped)
+  // the window's sources (the item's window: cells i0 - 2 .. i0 + W + 1, boundary-mapped)
   ClusterWin<SL> tab;
 #pragma unroll
   for (int s = 0; s < SL; ++s) {
@@ -232,8 +248,8 @@ __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps
     tab.widx[s] = -1;
     tab.neg[s] = false;
     for (int b = 0; b < 3; ++b) tab.src[b][s] = nullptr;
-    if (q < NA * (BW + 2)) {
-      const int a = q / (BW + 2), col = q - a * (BW + 2);
+    if (q < NA * WC) {
+      const int a = q / WC, col = q - a * WC;
       int flip;
       const int ii = bc_map(i0 - 2 + col, nx, A.P.bc[0], A.P.bc[1], flip);
       const int owner = ii / W;
@@ -259,7 +275,8 @@ __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps
       Cluster1D<NA, W, SL, R> io{st, vhs, &amax[k][0], &bad[k][0], &tab, k - 1, k % 3, k, i0,
                                  scl.dt, scl.alpha[k - 1][0]};
       if (t == 0) bad[k][0] = 0u;
-      stage1d_item_io<EQ, CHAR, R, BW>(A.P, io, rank);
+      if constexpr (FIELDS) stage1d_fields_item_io<R, BW>(A.P, io, rank);
+      else stage1d_item_io<EQ, CHAR, R, BW>(A.P, io, rank);
     }
   }
   for (int q = t; q < NA * W; q += BW) {
@@ -272,7 +289,7 @@ __global__ void __launch_bounds__(32) step1d_cluster_kernel(Step1D A, int nsteps
 
 // Largest cluster (CTAs) the device runs for this kernel: 16 where non-portable cluster sizes
 // are allowed and a 16-CTA cluster fits, else 8; 0 if clusters are not available.
-template <int EQ, bool CHAR, typename R>
+template <int EQ, bool CHAR, typename R, bool FIELDS>
 static int cluster_max() {
   static int cache[64] = {};
   int dev = 0;
@@ -282,13 +299,13 @@ static int cluster_max() {
   cudaDeviceGetAttribute(&cc, cudaDevAttrComputeCapabilityMajor, dev);
   int best = -1;
   if (cc >= 9) {
-    auto kern = step1d_cluster_kernel<EQ, CHAR, R>;
+    auto kern = step1d_cluster_kernel<EQ, CHAR, R, FIELDS>;
     best = 8;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
         cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
-      cfg.blockDim = dim3(32);
+      cfg.blockDim = dim3(kClusterBW<FIELDS>);
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = 16;
@@ -305,11 +322,11 @@ static int cluster_max() {
   return best > 0 ? best : 0;
 }
 
-template <int EQ, bool CHAR, typename R>
+template <int EQ, bool CHAR, typename R, bool FIELDS>
 static cudaError_t cluster_launch(const Step1D& A, int nsteps, int nb, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nb);
-  cfg.blockDim = dim3(32);
+  cfg.blockDim = dim3(kClusterBW<FIELDS>);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute at[1];
@@ -319,7 +336,22 @@ static cudaError_t cluster_launch(const Step1D& A, int nsteps, int nb, cudaStrea
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, step1d_cluster_kernel<EQ, CHAR, R>, A, nsteps);
+  return cudaLaunchKernelEx(&cfg, step1d_cluster_kernel<EQ, CHAR, R, FIELDS>, A, nsteps);
+}
+
+// 1D Euler with the characteristic decomposition on a grid short enough for one cluster: the
+// default layout (no tuning-table entry) is one lane per characteristic field in 128-thread
+// blocks of 30 cells, in the per-stage, the cooperative and the cluster-resident launches
+// alike (so hweno_step and hweno_advance give the same bits).
+template <int EQ, bool CHAR, typename R>
+static bool short_fields1d(int nx) {
+  if constexpr (EQ == EQ_EULER && CHAR) {
+    const int m = cluster_max<EQ, CHAR, R, true>();
+    return m > 0 && (nx + kClusterW - 1) / kClusterW <= m;
+  } else {
+    (void)nx;
+    return false;
+  }
 }
 
 template <int EQ, bool CHAR, typename R, int BW, bool FIELDS>
@@ -343,10 +375,18 @@ static cudaError_t steps1d_t(const Step1D& A, int nsteps, cudaStream_t st) {
   TileShape ts = tuning_shape(EQ, CHAR ? 1 : 0, sizeof(R) == 4 ? 1 : 0, nx, 1);
   // a grid that fits one cluster runs resident in it, unless the autotuner chose a layout
   // (a cluster launch the device refuses -- no room for the cluster at the time -- falls
-  // back to the cooperative launch)
+  // back to the cooperative launch of the same layout)
   const int nb = (nx + kClusterW - 1) / kClusterW;
-  if (ts.width == 0 && ts.lanes == 0 && nb <= cluster_max<EQ, CHAR, R>()) {
-    if (cluster_launch<EQ, CHAR, R>(A, nsteps, nb, st) == cudaSuccess) return cudaSuccess;
+  const bool untuned = ts.width == 0 && ts.lanes == 0;
+  if constexpr (EQ == EQ_EULER && CHAR) {
+    if (untuned && short_fields1d<EQ, CHAR, R>(nx)) {
+      if (cluster_launch<EQ, CHAR, R, true>(A, nsteps, nb, st) == cudaSuccess) return cudaSuccess;
+      cudaGetLastError();
+      return coop_launch<EQ, CHAR, R, 128, true>(A, nsteps, (nx + 29) / 30, st);
+    }
+  }
+  if (untuned && nb <= cluster_max<EQ, CHAR, R, false>()) {
+    if (cluster_launch<EQ, CHAR, R, false>(A, nsteps, nb, st) == cudaSuccess) return cudaSuccess;
     cudaGetLastError();
   }
   if constexpr (EQ == EQ_EULER && CHAR) {

@@ -224,8 +224,8 @@ __device__ __forceinline__ void stage1d_item(const KProblem& P, const KStage& S,
 // serial FP64 work -- three field reconstructions one after the other in stage1d_item --
 // is split over three lanes, which shortens the dependent chain of a warp for grids too
 // short to fill the GPU with one thread per cell.  Every lane of a warp runs every shuffle.
-template <typename R, int BW>
-__device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KStage& S, int blk) {
+template <typename R, int BW, class IO>
+__device__ __forceinline__ void stage1d_fields_item_io(const KProblem& P, const IO& io, int blk) {
   constexpr int NC = 3, NM = 2, G = BW / 4;
   const int nx = P.nx;
   const int t = threadIdx.x, q = t >> 2, f = t & 3;
@@ -238,14 +238,18 @@ __device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KSt
   __shared__ R fhat[NC][G + 1];       // flux at the left face of slot q's cell
   __shared__ double red[BW / 32];
 
-  for (int idx = t; idx < NC * NM * (G + 2); idx += BW) {
-    const int a = idx / (G + 2), col = idx % (G + 2);
-    const int c = a / NM, m = a % NM;
-    int flip;
-    const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
-    double val = S.Uin[(size_t)a * nx + ii];
-    if (flip) val *= mirror_sign<EQ_EULER, 1>(c, m, 1, 0);
-    win[a][col] = from_f64<R>(val);
+  if constexpr (IO::kTabulated) {
+    io.fill(&win[0][0]);
+  } else {
+    for (int idx = t; idx < NC * NM * (G + 2); idx += BW) {
+      const int a = idx / (G + 2), col = idx % (G + 2);
+      const int c = a / NM, m = a % NM;
+      int flip;
+      const int ii = bc_map(i0 - 2 + col, nx, P.bc[0], P.bc[1], flip);
+      double val = io.in(a, ii);
+      if (flip) val *= mirror_sign<EQ_EULER, 1>(c, m, 1, 0);
+      win[a][col] = from_f64<R>(val);
+    }
   }
   __syncthreads();
 
@@ -283,7 +287,7 @@ __device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KSt
   }
   __syncthreads();
   // LF flux at the right face of the slot's cell, component f (Eq. 2.4), once per face
-  const R alpha = (R)S.alpha_in[0];
+  const R alpha = (R)io.alpha();
   if (need && f < NC && q < G - 1 && i < nx) {
     const R uL = pts[3][f], fL = fp[3][f];
     const R uR = trL[f][0][q + 1], fR = trL[f][1][q + 1];
@@ -294,31 +298,31 @@ __device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KSt
   double ou = 0.0, ov = 0.0;
   bool bad = false;
   if (upd && f < NC) {
-    const double dt = *S.dt;
+    const double dt = io.dt();
+    const int k = io.k();
     const R idx = kconst<R>(P.inv_dx, P.inv_dxf);
     const R fL = fhat[f][q], fR = fhat[f][q + 1];
     const R F1 = -(fR - fL) * idx;
     const R vol = R(1.0 / 12.0) * (fp[0][f] + fp[3][f]) + R(5.0 / 12.0) * (fp[1][f] + fp[2][f]);
     const R F2 = (vol - R(0.5) * (fL + fR)) * idx;
     const double own_u = (sizeof(R) == sizeof(double)) ? to_f64(win[f * NM][q + 1])
-                                                        : S.Uin[(size_t)(f * NM) * nx + i];
+                                                        : io.in(f * NM, i);
     const double own_v = to_f64(vh[f]);
-    const size_t q0 = (size_t)(f * NM) * nx + i, q1 = q0 + nx;
     double base_u, base_v;
-    if (S.k == 1) {
+    if (k == 1) {
       base_u = own_u;
       base_v = own_v;
-      S.Vh[(size_t)f * nx + i] = own_v;
+      io.set_vh(f, i, own_v);
     } else {
-      base_u = S.Un[q0];
-      base_v = S.Vh[(size_t)f * nx + i];
+      base_u = io.un(f * NM, i);
+      base_v = io.vh(f, i);
     }
     const double au = fma(dt, to_f64(F1), own_u), av = fma(dt, to_f64(F2), own_v);
-    if (S.k == 1) { ou = au; ov = av; }
-    else if (S.k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
+    if (k == 1) { ou = au; ov = av; }
+    else if (k == 2) { ou = fma(0.75, base_u, 0.25 * au); ov = fma(0.75, base_v, 0.25 * av); }
     else { ou = fma(1.0 / 3.0, base_u, 2.0 / 3.0 * au); ov = fma(1.0 / 3.0, base_v, 2.0 / 3.0 * av); }
-    S.Uout[q0] = ou;
-    S.Uout[q1] = ov;
+    io.out(f * NM, i, ou);
+    io.out(f * NM + 1, i, ov);
     bad = !finite_bits(ou) || !finite_bits(ov);
   }
   // wave speed and physicality of the output average: the slot's three components
@@ -335,7 +339,7 @@ __device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KSt
   bad = __shfl_sync(0xffffffffu, (int)bad, lane0) | __shfl_sync(0xffffffffu, (int)bad, lane0 + 1) |
         __shfl_sync(0xffffffffu, (int)bad, lane0 + 2);
   if (upd && f == 0 && bad) {
-    atomicOr(S.status, kStatusNonphysical);
+    io.nonphysical();
     wmax = 0.0;
   }
 #pragma unroll
@@ -346,9 +350,15 @@ __device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KSt
     double m = red[0];
 #pragma unroll
     for (int w = 1; w < BW / 32; ++w) m = fmax(m, red[w]);
-    atomic_max_nonneg(&S.alpha_out[0], m);
+    io.raise_alpha(m);
   }
   __syncthreads();  // the block may start another item in the same shared memory
+}
+
+template <typename R, int BW>
+__device__ __forceinline__ void stage1d_fields_item(const KProblem& P, const KStage& S, int blk) {
+  const Global1D io{S, P.nx};
+  stage1d_fields_item_io<R, BW>(P, io, blk);
 }
 
 }  // namespace hw

@@ -106,7 +106,9 @@ def test_stage_2d_edge_sizes(nx, ny):
 
 @pytest.mark.parametrize("n", [2, 3, 29, 30, 31, 61, 125, 126, 127, 253, 40001])
 def test_stage_1d_edge_sizes(n):
-    """Short grids run in one-warp blocks of 30 cells (multiples and +-1 of that width); a grid
+    """Short grids run in blocks of 30 cells (one-warp blocks of one thread per cell; for 1D
+    Euler with the characteristic decomposition on grids of at most one cluster, 128-thread
+    blocks of one lane per characteristic field): multiples and +-1 of that width; a grid
     long enough to give every SM a 128-thread block (40001 cells) runs in those."""
     op, hp = problems(1, "euler", n, bc=1)
     _check_stage(op, hp, 3, seed=7)
