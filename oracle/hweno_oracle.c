@@ -20,8 +20,10 @@
  *     reconstructing cell's own average; in 2D two passes (x: df/dU, y: dg/dU); the x pass
  *     gives the x-edge points, the interior points used in f and v-hat, the y pass the
  *     y-edge points, the interior points used in g and w-hat; u_ave uses the
- *     characteristic averages.  Parity unpinned against the paper (its figures are not
- *     available); pinned only by invariants (constant states, symmetry, convergence).
+ *     characteristic averages.  Pinned against the paper by Table 3.6 (Example 3.4 at the
+ *     wavenumber whose errors the table prints: this decomposition with the scale-invariant
+ *     weights reproduces them, the component-wise reconstruction and the original weights
+ *     do not) and by invariants (constant states, symmetry, convergence).
  *   - alpha of the global LF flux: max over the cell averages of the stage input
  *     (per direction), recomputed every stage.
  *   - time step: cfl*dx/alpha (1D), cfl/(alpha1/dx + alpha2/dy) (2D), from U^n.

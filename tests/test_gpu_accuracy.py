@@ -101,6 +101,36 @@ def test_euler_2d_table_3_6(n):
     assert 0.55 < e.max() / g["linf"] < 1.3
 
 
+@pytest.mark.parametrize("n", [80, 120])
+def test_table_3_6_singles_out_the_characteristic_scale_invariant_weights(n):
+    """The Table 3.6 errors pin the characteristic reading of Remark 2.2 (u_ave from the
+    characteristic averages): at the half wavenumber with dt = 0.02 dx, the scale-invariant
+    weights with the characteristic decomposition come to 0.64-0.69 of the printed L1 and
+    Linf, while the component-wise reconstruction (u_ave from the conserved averages) and the
+    original weights (u_ave = 1) stay at 0.23-0.41 of them (measured)."""
+    g = _golden()["table_3_6_euler_2d"][str(n)]
+    w = I.euler_density_wave_2d(n, k=0.5)
+    ex = I.euler_density_wave_exact_2d(n, 2.0, k=0.5)[0, 0]
+
+    def ratios(weights, characteristic):
+        p = H.make_problem(dim=2, equation=H.HWENO_EULER, nx=n, ny=n, x0=0, x1=4, y0=0, y1=4,
+                           dt_fixed=0.02 * 4.0 / n, weights=weights,
+                           characteristic=characteristic)
+        eng = H.hweno_create()
+        try:
+            sid = H.hweno_open(eng, p, w.U0)
+            H.hweno_advance(eng, sid, 2.0)
+            U, _ = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
+        finally:
+            H.hweno_destroy(eng)
+        e = np.abs(U[0, 0] - ex)
+        return e.mean() / g["l1"], e.max() / g["linf"]
+    char = ratios(H.HWENO_W_SCALE_INVARIANT, 1)
+    assert min(char) > 0.55
+    for other in (ratios(H.HWENO_W_SCALE_INVARIANT, 0), ratios(H.HWENO_W_ORIGINAL, 1)):
+        assert max(other) < 0.5
+
+
 def test_euler_2d_density_wave_converges():
     """Example 3.4 at T = 0.5 with dt ~ dx^(5/3): L1 order of the finest pair >= 5."""
     errs = []
