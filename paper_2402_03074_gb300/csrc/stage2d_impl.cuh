@@ -18,18 +18,29 @@ __global__ void __launch_bounds__(BW, kMinBlocks2D<R, BW>)
   extern __shared__ double smem[];
   __shared__ double red[2][BW / 32];
   const int ny = P.ny;
+  // the block's pieces: one (band, row chunk), or the pieces of its segment; one call site of
+  // the (large, inlined) work item
+  int band, j0, j1;
+  long long q = 0, qend = 0;
   if (seg == 0) {
-    const int j0 = blockIdx.y * rows;
-    stage2d_item<EQ, CHAR, R, BW>(P, S, blockIdx.x, j0, min(ny, j0 + rows), wout, smem, red);
-    return;
+    band = blockIdx.x;
+    j0 = blockIdx.y * rows;
+    j1 = min(ny, j0 + rows);
+  } else {
+    q = (long long)blockIdx.x * seg;
+    qend = min(q + seg, (long long)bands * ny);
+    band = (int)(q / ny);
+    j0 = (int)(q - (long long)band * ny);
+    j1 = (int)min((long long)ny, (long long)j0 + (qend - q));
+    q += j1 - j0;
   }
-  long long q = (long long)blockIdx.x * seg;
-  const long long qend = min(q + seg, (long long)bands * ny);
 #pragma unroll 1
-  while (q < qend) {  // uniform over the block
-    const int band = (int)(q / ny), j0 = (int)(q - (long long)band * ny);
-    const int j1 = (int)min((long long)ny, (long long)j0 + (qend - q));
+  for (;;) {  // uniform over the block
     stage2d_item<EQ, CHAR, R, BW>(P, S, band, j0, j1, wout, smem, red);
+    if (q >= qend) break;
+    band = (int)(q / ny);
+    j0 = (int)(q - (long long)band * ny);
+    j1 = (int)min((long long)ny, (long long)j0 + (qend - q));
     q += j1 - j0;
   }
 }
