@@ -52,15 +52,15 @@ FP32_PEAK_TFLOPS_FALLBACK = 74.2
 # flop rate.
 FP64_OPS_PER_CELL_STAGE = 3351.0
 # DRAM bytes read + written by the same launch (ncu)
-FP64_STAGE_DRAM_BYTES = 524.4e6 + 725.1e6
+FP64_STAGE_DRAM_BYTES = 523.6e6 + 708.3e6
 # FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
-FP64_PIPE_UTIL_NCU = 0.839
+FP64_PIPE_UTIL_NCU = 0.843
 # FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (928 per
 # reconstructed cell less 2.9 % ring redundancy at three blocks per SM), FP32 flops, and the
 # launch's DRAM bytes
 FP32BULK_FP64_OPS_PER_CELL_STAGE = 902.0
 FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 3971.0
-FP32BULK_STAGE_DRAM_BYTES = 468.2e6 + 1088.6e6
+FP32BULK_STAGE_DRAM_BYTES = 460.9e6 + 1051.2e6
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
