@@ -422,19 +422,36 @@ cudaError_t launch_steps1d(int eq, bool characteristic, bool mixed, const Step1D
                : steps1d_t<EQ_EULER, false, double>(A, nsteps, st);
 }
 
+// the largest stack frame of a kernel list; false if an attribute query fails
+template <typename... K>
+static bool local_max(size_t* m, K... kern) {
+  bool ok = true;
+  auto one = [&](auto k) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) ok = false;
+    else if (fa.localSizeBytes > *m) *m = fa.localSizeBytes;
+  };
+  (one(kern), ...);
+  return ok;
+}
+
+// the largest stack frame among the class's per-stage, cooperative and cluster-resident
+// kernels (0 if an attribute query fails)
 template <int EQ, bool CHAR, typename R>
 static size_t local1d_t() {
-  cudaFuncAttributes fa, fb;
-  if (cudaFuncGetAttributes(&fa, stage1d_kernel<EQ, CHAR, R, 128>) != cudaSuccess) return 0;
-  if (cudaFuncGetAttributes(&fb, stage1d_kernel<EQ, CHAR, R, 32>) != cudaSuccess) return 0;
-  size_t m = fa.localSizeBytes > fb.localSizeBytes ? fa.localSizeBytes : fb.localSizeBytes;
+  size_t m = 0;
+  if (!local_max(&m, stage1d_kernel<EQ, CHAR, R, 128>, stage1d_kernel<EQ, CHAR, R, 32>,
+                 step1d_coop_kernel<EQ, CHAR, R, 128, false>,
+                 step1d_coop_kernel<EQ, CHAR, R, 32, false>,
+                 step1d_cluster_kernel<EQ, CHAR, R, false>))
+    return 0;
   if constexpr (EQ == EQ_EULER && CHAR) {
-    cudaFuncAttributes f1, f2, f3;
-    if (cudaFuncGetAttributes(&f1, stage1d_fields_kernel<R, 32>) != cudaSuccess ||
-        cudaFuncGetAttributes(&f2, stage1d_fields_kernel<R, 64>) != cudaSuccess ||
-        cudaFuncGetAttributes(&f3, stage1d_fields_kernel<R, 128>) != cudaSuccess)
+    if (!local_max(&m, stage1d_fields_kernel<R, 32>, stage1d_fields_kernel<R, 64>,
+                   stage1d_fields_kernel<R, 128>, step1d_coop_kernel<EQ, CHAR, R, 32, true>,
+                   step1d_coop_kernel<EQ, CHAR, R, 64, true>,
+                   step1d_coop_kernel<EQ, CHAR, R, 128, true>,
+                   step1d_cluster_kernel<EQ, CHAR, R, true>))
       return 0;
-    for (size_t x : {f1.localSizeBytes, f2.localSizeBytes, f3.localSizeBytes}) m = x > m ? x : m;
   }
   return m;
 }
