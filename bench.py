@@ -748,7 +748,8 @@ def run_paper_tables(args):
          lambda t: I.euler_density_wave_exact_1d(n, t), 1.34e01),
         ("Table 3.4, 2D Burgers", I.burgers_sine_2d(n), H.HWENO_BURGERS,
          lambda t: I.burgers_exact_2d(n, t), 3.69e02),
-        # the wavenumber whose errors Table 3.6 prints (sin(pi (x + y) / 2); R20)
+        # the wavenumber whose errors Table 3.6 prints: sin(pi (x + y) / 2), not the
+        # sin(pi (x + y)) of the example's text
         ("Table 3.6, 2D Euler", I.euler_density_wave_2d(n, k=0.5), H.HWENO_EULER,
          lambda t: I.euler_density_wave_exact_2d(n, t, k=0.5), 2.14e05),
     ]
@@ -793,7 +794,7 @@ def run_dt_sweep(args):
               lambda n, t: I.burgers_exact_2d(n, t), "table_3_4_burgers_2d",
               ("scale-invariant", "linear")) for n in (40, 80, 120)]
     # Example 3.4 at the printed wavenumber sin(pi (x + y)) and at sin(pi (x + y) / 2), whose
-    # errors Table 3.6 prints (R20)
+    # errors Table 3.6 prints
     for kk in (1.0, 0.5):
         cases += [(f"Table 3.6, 2D Euler, k = {kk}", H.HWENO_EULER, n,
                    I.euler_density_wave_2d(n, k=kk),
@@ -830,7 +831,7 @@ def run_sweep(args):
     """Convergence of the FP64 and FP32-bulk paths on the periodic isentropic vortex
     (rho = p = 1, u = v = 1 plus the vortex, [0,1]^2, T = 0.05) against the exact translated
     solution, N = 128 .. 2048; dt = 0.6 dx / 4 (N0 / N)^(2/3) so that the RK3 error does not
-    mask fifth order (R8 reading)."""
+    mask fifth order (the paper fixes only CFL 0.6)."""
     import torch
     from paper_2402_03074_gb300 import build as B
     B.build()

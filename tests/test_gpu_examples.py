@@ -7,7 +7,7 @@ nonlinear weights at the shock fronts carry the difference, and it grows by a fe
 per step; in the Sedov problem the oracle's solution even loses its mirror symmetry this
 way).  The GPU path evaluates the same formulas in another order with FMA contraction
 (per-stage parity 1e-12 elsewhere), so over a whole run it can only be held to the same
-sensitivity (R15: for discontinuous runs the deviation is reported): both sides finish with
+sensitivity (for discontinuous runs the deviation is reported, not bounded at 1e-12): both sides finish with
 positive states and the same number of steps (+-1 where the deviation reaches the wave
 speeds), and the GPU run differs from the oracle's by at most ten times what a 1-ulp
 perturbation of the data does to the oracle's own run."""
