@@ -1,6 +1,6 @@
 """ctypes wrapper of the FP64 CPU oracle (hweno_oracle.c).
 
-TEST INFRASTRUCTURE ONLY: this package is the checker of the CUDA path.  Only tests/,
+TEST INFRASTRUCTURE ONLY: this package is the oracle of the CUDA path.  Only tests/,
 __graft_entry__.smoke() and bench.py's cpu_baseline / reference legs import it; the
 product package (paper_2402_03074_gb300) never does, and this package never imports the
 product.  It follows the paper (arXiv 2402.03074) step by step; see hweno_oracle.c for the

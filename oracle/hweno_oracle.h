@@ -3,7 +3,7 @@
  * Fan, Qiu and Zhao, "A moment-based Hermite WENO scheme with unified stencils for
  * hyperbolic conservation laws" (arXiv 2402.03074).
  *
- * TEST INFRASTRUCTURE ONLY.  This library is the checker against which the CUDA
+ * TEST INFRASTRUCTURE ONLY.  This library is the oracle against which the CUDA
  * path is compared.  It is called by tests/, by __graft_entry__.smoke() and by the
  * cpu_baseline / reference legs of bench.py, and by nothing else.  It shares no code,
  * header, table or helper with the CUDA library (include/hweno.h); the only thing the
