@@ -243,9 +243,12 @@ int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
    candidates are the block width (128 or 32 threads) and the threads per cell (one per cell,
    or -- Euler with the characteristic decomposition -- one lane per characteristic field in
    blocks of 128, 64 or 32 threads); *best_rows receives the block width and *best_bands the
-   threads per cell (1 or 4).  Output pointers may be NULL.  The 2D tile shape changes no
-   result bit (every cell and face is computed by the same code in any decomposition); the
-   1D lanes-per-field layout computes the same formulas, equal within rounding. */
+   threads per cell (1 or 4).  Output pointers may be NULL.  The 2D bands and rows change no
+   result bit (every cell and face is computed by the same code in any decomposition), nor
+   does the block width, except for FP64 Euler with the characteristic decomposition, whose
+   96-thread blocks form the Appendix coefficients of the conserved components once per cell
+   and project them per pass (the same formulas, equal within rounding); the 1D
+   lanes-per-field layout computes the same formulas, equal within rounding. */
 int hweno_autotune(hweno_engine* eng, const hweno_problem* p, const double* moments_host,
                    int* best_rows, int* best_bands, double* best_ms);
 /* Save the tuning table as text (one entry per line, with the GPU name); load it back
