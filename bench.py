@@ -295,7 +295,8 @@ def run_ours(args):
     elif not args.no_autotune:
         for name, prec in (("fp64", H.HWENO_FP64), ("mixed32", H.HWENO_MIXED32)):
             r, b, ms = H.hweno_autotune(eng, prob(prec), U0)
-            tiles[name] = {"rows": r, "bands": b, "stage_ms": ms}
+            tq = H.hweno_tuning_query(prob(prec)) or {}
+            tiles[name] = {"rows": r, "bands": b, "width": tq.get("width", 0), "stage_ms": ms}
         if args.save_tuning:
             H.hweno_tuning_save(args.save_tuning)
 

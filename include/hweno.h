@@ -232,14 +232,16 @@ int hweno_stage_batch_static(int n, const hweno_problem* problems, int k,
 
 /* ---- launch-geometry autotuner -------------------------------------------------------- */
 /* Time one fused stage launch of the 2D problem p on a scratch copy of moments_host for each
-   candidate tile shape -- the block width (128, 96 or 64 threads, one per column of a band
+   candidate tile shape -- the block width (128, 96, 64 or 192 threads, one per column of a band
    plus its two ring columns) x the number of bands the columns are split into (the default bands,
    and 1.25, 1.5 and 2 times as many as the widest bands of that width) x the height of the
    row chunks a block sweeps (the default one-wave geometry and 8, 16, 32, 64, 128, 256 rows)
-   -- keep the fastest in the process-wide tuning table (keyed by equation, characteristic
-   decomposition, precision and grid) for every later single-solve launch of such problems,
-   and report it (*best_rows, *best_bands: 0 = the default; *best_ms: one stage; the block
-   width through hweno_tuning_query).  For a 1D problem the
+   -- then time the closest candidates (at most four, within 3 % of the fastest) again over
+   whole three-stage sequences, keep the fastest sequence's shape in the process-wide tuning
+   table (keyed by equation, characteristic decomposition, precision and grid) for every
+   later single-solve launch of such problems, and report it (*best_rows, *best_bands: 0 =
+   the default; *best_ms: its mean stage time; the block width through hweno_tuning_query).
+   The scratch copy is stepped with dt = 0.  For a 1D problem the
    candidates are the block width (128 or 32 threads) and the threads per cell (one per cell,
    or -- Euler with the characteristic decomposition -- one lane per characteristic field in
    blocks of 128, 64 or 32 threads); *best_rows receives the block width and *best_bands the
@@ -258,7 +260,7 @@ int hweno_tuning_load(const char* path);
 /* The tuning-table entry a single-solve launch of problem p would use: *rows, *bands (2D tile
    shape; 0 = the default, -1 = the default chosen by the autotuner; rows < -1: the bands'
    rows swept in segments of -rows band-rows, one per block), *width (block width: 2D
-   128, 96 or 64, 1D 128, 64 or 32; 0 = the default) and *lanes (1D threads per cell).  Returns 1
+   128, 96, 64 or 192, 1D 128, 64 or 32; 0 = the default) and *lanes (1D threads per cell).  Returns 1
    when the table has an entry for p, 0 when not (all outputs 0), HWENO_ERR_ARG for a NULL or
    malformed p.  Output pointers may be NULL. */
 int hweno_tuning_query(const hweno_problem* p, int* rows, int* bands, int* width, int* lanes);

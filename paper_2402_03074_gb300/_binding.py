@@ -264,7 +264,7 @@ def hweno_engine_stream(eng) -> int:
 # ---- launch-geometry autotuner --------------------------------------------------------
 def hweno_autotune(eng, p: hweno_problem, U: np.ndarray):
     """Returns (best rows per chunk, best band count (0 = the defaults), milliseconds of one
-    stage)."""
+    stage: in 2D the mean stage of the fastest three-stage sequence)."""
     U = np.ascontiguousarray(U, dtype=np.float64)
     rows = ctypes.c_int()
     bands = ctypes.c_int()

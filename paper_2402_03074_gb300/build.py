@@ -13,8 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhweno.so")
-SOURCES = ["stage2d.cu", "stage2d_w96.cu", "stage2d_w64.cu", "stage1d.cu", "batch.cu",
-           "static_batch.cu", "engine.cu", "server.cu", "tune.cu", "peaks.cu"]
+SOURCES = ["stage2d.cu", "stage2d_w96.cu", "stage2d_w64.cu", "stage2d_w192.cu", "stage1d.cu",
+           "batch.cu", "static_batch.cu", "engine.cu", "server.cu", "tune.cu", "peaks.cu"]
 HEADERS = ["hweno_device.cuh", "launch.h", "server.h", "batch.h", "geometry.h",
            "stage1d_item.cuh", "stage2d_item.cuh", "stage2d_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

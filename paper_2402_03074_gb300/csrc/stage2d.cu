@@ -19,6 +19,7 @@ cudaError_t launch_stage2d(int eq, bool characteristic, bool mixed, const KProbl
   const int w = t.width > 0 ? t.width : default_width2d(eq, ch, mixed);
   if (w == 64) return launch2d_width<64>(eq, ch, mixed, P, S, t, st);
   if (w == 96) return launch2d_width<96>(eq, ch, mixed, P, S, t, st);
+  if (w == 192) return launch2d_width<192>(eq, ch, mixed, P, S, t, st);
   return launch2d_width<128>(eq, ch, mixed, P, S, t, st);
 }
 
@@ -29,6 +30,8 @@ cudaError_t prepare_stage2d(size_t* max_local) {
   if (e == cudaSuccess) e = prepare2d_width<96>(&l);
   m = l > m ? l : m;
   if (e == cudaSuccess) e = prepare2d_width<64>(&l);
+  m = l > m ? l : m;
+  if (e == cudaSuccess) e = prepare2d_width<192>(&l);
   m = l > m ? l : m;
   if (max_local) *max_local = m;
   return e;

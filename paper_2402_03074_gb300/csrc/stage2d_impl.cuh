@@ -1,6 +1,7 @@
 // stage2d_impl.cuh -- the single-solve 2D stage kernel and its launch for one block width,
-// instantiated per width in stage2d.cu (128 threads), stage2d_w96.cu and stage2d_w64.cu so the
-// widths compile in parallel; the dispatch over widths and classes is in stage2d.cu.
+// instantiated per width in stage2d.cu (128 threads), stage2d_w96.cu, stage2d_w64.cu and
+// stage2d_w192.cu so the widths compile in parallel; the dispatch over widths and classes is
+// in stage2d.cu.
 #pragma once
 #include "geometry.h"
 #include "launch.h"
@@ -102,6 +103,7 @@ cudaError_t prepare2d_width(size_t* max_local);
 HW_STAGE2D_DECLARE(128)
 HW_STAGE2D_DECLARE(96)
 HW_STAGE2D_DECLARE(64)
+HW_STAGE2D_DECLARE(192)
 #undef HW_STAGE2D_DECLARE
 
 #define HW_STAGE2D_WIDTH(BW)                                                                  \

@@ -18,10 +18,10 @@ namespace hw {
 
 
 // Resident blocks per SM the 2D stage kernels are compiled for: the FP64 kernels take the
-// whole register file at eight warps per SM (255 registers per thread: two 128-thread or four
-// 64-thread blocks), the FP32-bulk kernels twelve warps (at most 168 registers per thread, a
-// few hundred bytes of spills: three 128-thread or six 64-thread blocks), which hides more of
-// the FP64 latency of their weight evaluation.
+// whole register file at 255 registers per thread (one 128- or 192-thread block, two of 96
+// threads, four of 64), the FP32-bulk kernels twelve warps (at most 168 registers per thread:
+// two 192-thread, three 128-thread, four 96-thread or six 64-thread blocks), which hides more
+// of the FP64 latency of their weight evaluation.
 template <typename R, int BW>
 constexpr int kMinBlocks2D = sizeof(R) == 4 ? 384 / BW : (BW == 128 ? 1 : 256 / BW);
 

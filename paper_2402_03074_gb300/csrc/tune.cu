@@ -3,22 +3,26 @@
 // The 2D stage kernel's blocks sweep row chunks of a band.  The tile shape trades redundant
 // work against balance and latency hiding: taller chunks waste fewer ring rows, narrower
 // bands more ring columns and lanes, the tile count sets how evenly the blocks fill the SMs,
-// and the block width (64, 96 or 128 threads) sets the resident warps per SM and the idle
+// and the block width (64, 96, 128 or 192 threads) sets the resident warps per SM and the idle
 // lanes of a band (the 96-thread characteristic FP64 kernel also forms the coefficients once
 // per cell).  The autotuner times one stage launch of a problem for each candidate shape
-// (block width x band count x chunk height) on a scratch copy of the caller's moments, keeps
-// the fastest in a process-wide table keyed by (equation, characteristic decomposition,
-// precision, grid), and the table is consulted by every later single-solve launch of such a
-// problem (the batched launches size their work items from the load instead).  The table can
-// be saved and loaded as text; entries carry the GPU name.
+// (block width x band count x chunk height) on a scratch copy of the caller's moments (with
+// dt = 0, so the copy does not evolve), times the closest few again over whole three-stage
+// sequences, and keeps the fastest in a process-wide table keyed by (equation,
+// characteristic decomposition, precision, grid); the table is consulted by every later
+// single-solve launch of such a problem (the batched launches size their work items from the
+// load instead).  The table can be saved and loaded as text; entries carry the GPU name.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <utility>
+#include <vector>
 
 #include "../../include/hweno.h"
 #include "launch.h"
@@ -136,19 +140,43 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
     if (rc) engine_set_error(e, "autotune launch failed");
     return rc;
   }
-  // candidates: block widths (128, 96 and 64 threads) x band counts (0 = the default bands; then
-  // 1.25, 1.5 and 2 times as many as the widest bands) x chunk heights (0 = one wave over the
-  // resident slots)
+  // candidates: block widths (128, 96, 64 and 192 threads) x band counts (0 = the default bands; then
+  // 1.25, 1.5 and 2 times as many as the widest bands of that width) x chunk heights (0 = one
+  // wave over the resident slots).  Screened on stage 1 (the fastest of three launches after
+  // one untimed); the finalists -- at most four, within 3 % of the fastest -- are then timed
+  // over whole three-stage sequences (stages 2 and 3 also read U^n and V-hat), and the fastest
+  // sequence decides.
   const int rows_c[] = {0, 8, 16, 32, 64, 128, 256};
-  const int widths[] = {128, 96, 64};
+  const int widths[] = {128, 96, 64, 192};
+  constexpr int kWidths = sizeof(widths) / sizeof(widths[0]);
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  TileShape best;
-  float best_t = 1e30f;
-  const KStage S = solve_stage(s, 1);
+  const KStage S3[3] = {solve_stage(s, 1), solve_stage(s, 2), solve_stage(s, 3)};
   const KProblem kp = solve_kproblem(s);
-  for (int wi = 0; wi < 3 && rc == HWENO_OK; ++wi) {
+  const bool ch = p->equation == HWENO_EULER && p->characteristic;
+  const bool mixed = p->precision == HWENO_MIXED32;
+  // the fastest of reps - 1 timed runs (after one untimed) of the stages k0 .. k1 in shape t,
+  // per stage; < 0 on a launch error
+  auto time_shape = [&](const TileShape& t, int k0, int k1, int reps) -> float {
+    tuning_force_shape(t);
+    float tmin = 1e30f;
+    for (int rep = 0; rep < reps; ++rep) {
+      cudaEventRecord(a, st);
+      cudaError_t c = cudaSuccess;
+      for (int k = k0; k <= k1 && c == cudaSuccess; ++k)
+        c = launch_stage2d(p->equation, ch, mixed, kp, S3[k - 1], st);
+      cudaEventRecord(b, st);
+      if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) return -1.f;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      ms /= (float)(k1 - k0 + 1);
+      if (rep > 0 && ms < tmin) tmin = ms;
+    }
+    return tmin;
+  };
+  std::vector<std::pair<float, TileShape>> screened;
+  for (int wi = 0; wi < kWidths && rc == HWENO_OK; ++wi) {
     const int bw = widths[wi];
     const int bmin = (p->nx + bw - 3) / (bw - 2);
     const int bands_c[4] = {0, (5 * bmin + 3) / 4, (3 * bmin + 1) / 2, 2 * bmin};
@@ -161,29 +189,32 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
         t.rows = r > 0 ? r : -1;
         t.bands = bc > 0 ? bc : -1;
         t.width = bw;
-        tuning_force_shape(t);
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
-          cudaEventRecord(a, st);
-          cudaError_t c = launch_stage2d(p->equation,
-                                         p->equation == HWENO_EULER && p->characteristic,
-                                         p->precision == HWENO_MIXED32, kp, S, st);
-          cudaEventRecord(b, st);
-          if (c != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
-            rc = HWENO_ERR_CUDA;
-            break;
-          }
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, a, b);
-          if (rep > 0 && ms < tmin) tmin = ms;
+        const float ms = time_shape(t, 1, 1, 4);
+        if (ms < 0.f) {
+          rc = HWENO_ERR_CUDA;
+          break;
         }
-        if (rc) break;
-        if (tmin < best_t) {
-          best_t = tmin;
-          best.rows = r;
-          best.bands = bc;
-          best.width = bw;
-        }
+        screened.push_back({ms, t});
+      }
+    }
+  }
+  TileShape best;
+  float best_t = 1e30f;
+  if (rc == HWENO_OK && !screened.empty()) {
+    std::stable_sort(screened.begin(), screened.end(),
+                     [](const std::pair<float, TileShape>& x,
+                        const std::pair<float, TileShape>& y) { return x.first < y.first; });
+    const float lim = screened[0].first * 1.03f;
+    for (size_t i = 0; i < screened.size() && i < 4 && rc == HWENO_OK; ++i) {
+      if (i > 0 && screened[i].first > lim) break;
+      const float ms = time_shape(screened[i].second, 1, 3, 5);
+      if (ms < 0.f) {
+        rc = HWENO_ERR_CUDA;
+        break;
+      }
+      if (ms < best_t) {
+        best_t = ms;
+        best = screened[i].second;
       }
     }
   }
@@ -201,8 +232,8 @@ int hweno_autotune(hweno_engine* e, const hweno_problem* p, const double* host, 
   keep.width = best.width;
   tuning_set_shape(p->equation, p->equation == HWENO_EULER ? p->characteristic : 0,
                    p->precision == HWENO_MIXED32, p->nx, p->ny, keep);
-  if (best_rows) *best_rows = best.rows;
-  if (best_bands) *best_bands = best.bands;
+  if (best_rows) *best_rows = best.rows > 0 ? best.rows : 0;
+  if (best_bands) *best_bands = best.bands > 0 ? best.bands : 0;
   if (best_ms) *best_ms = best_t;
   return HWENO_OK;
 }

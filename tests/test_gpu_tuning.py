@@ -25,10 +25,11 @@ def test_autotune_keeps_results_and_roundtrips(tmp_path):
         H.hweno_close(eng, sid)
         rows, bands, ms = H.hweno_autotune(eng, p, w.U0)
         assert rows in (0, 8, 16, 32, 64, 128, 256) and ms > 0
-        # 256 columns: the widest bands are 3 (96- and 128-thread blocks) or 5 (64 threads)
-        assert bands in (0, 4, 5, 6, 7, 8, 10)
+        # 256 columns: the widest bands are 2 (192-thread blocks), 3 (96 and 128 threads) or
+        # 5 (64 threads)
+        assert bands in (0, 3, 4, 5, 6, 7, 8, 10)
         tq = H.hweno_tuning_query(p)
-        assert tq is not None and tq["width"] in (64, 96, 128) and tq["lanes"] == 0
+        assert tq is not None and tq["width"] in (64, 96, 128, 192) and tq["lanes"] == 0
         sid = H.hweno_open(eng, p, w.U0)
         H.hweno_advance(eng, sid, 1.0, max_steps=3)
         got, _ = H.hweno_get_state(eng, sid, np.empty_like(w.U0))
@@ -38,7 +39,7 @@ def test_autotune_keeps_results_and_roundtrips(tmp_path):
         # the default kernel's arithmetic: the tile decomposition does not change any bit
         np.testing.assert_array_equal(got, ref)
     else:
-        # 64 / 128 threads form the coefficients from the projected stencil: equal within
+        # 64 / 128 / 192 threads form the coefficients from the projected stencil: equal within
         # rounding to the 96-thread kernel, which projects the conserved coefficients
         S = np.abs(ref[:, 0]).max(axis=(1, 2)).reshape(-1, 1, 1, 1)
         assert float((np.abs(got - ref) / np.maximum(np.abs(ref), S)).max()) <= 1e-13
@@ -216,7 +217,7 @@ def test_autotune_1d_picks_a_layout_and_the_run_matches_oracle():
 
 
 # ------------------------------------------------------------------------------------------
-# 2D block widths (64, 96, 128 threads), selected through the tuning table
+# 2D block widths (64, 96, 128, 192 threads), selected through the tuning table
 def _tuning_file_2d(tmp_path, entries):
     import torch
     name = torch.cuda.get_device_name(0).replace(" ", "_")
@@ -228,7 +229,7 @@ def _tuning_file_2d(tmp_path, entries):
     return path
 
 
-@pytest.mark.parametrize("width", [64, 96, 128])
+@pytest.mark.parametrize("width", [64, 96, 128, 192])
 def test_block_widths_2d_match_oracle(tmp_path, width):
     """Characteristic FP64 2D Euler in every block width against the oracle at 1e-12 for every
     stage (the 96-thread kernel projects the conserved coefficients formed once per cell, the
@@ -254,14 +255,14 @@ def test_block_widths_2d_match_oracle(tmp_path, width):
 
 def test_block_widths_2d_same_bits_where_the_arithmetic_is_the_same(tmp_path):
     """The block width changes the decomposition, not the arithmetic, of the FP32-bulk kernel,
-    the component-wise FP64 kernel and the characteristic FP64 kernel in 64 and 128 threads:
-    their stage outputs are bitwise equal across widths."""
+    the component-wise FP64 kernel and the characteristic FP64 kernel in 64, 128 and 192
+    threads: their stage outputs are bitwise equal across widths."""
     from gpu_helpers import gpu_problems_stage
     nx, ny = 211, 17
     cases = [(1, 0), (0, 0), (1, 1)]   # (characteristic, mixed)
     for ch, mixed in cases:
         outs = {}
-        for width in (64, 96, 128):
+        for width in (64, 96, 128, 192):
             path = _tuning_file_2d(tmp_path, [(2, ch, mixed, nx, ny, width)])
             assert H.hweno_tuning_load(path) == 1
             try:
@@ -269,6 +270,7 @@ def test_block_widths_2d_same_bits_where_the_arithmetic_is_the_same(tmp_path):
             finally:
                 H.hweno_tuning_load(_tuning_file_2d(tmp_path, [(2, ch, mixed, nx, ny, 0)]))
         np.testing.assert_array_equal(outs[64], outs[128])
+        np.testing.assert_array_equal(outs[192], outs[128])
         if not (ch == 1 and mixed == 0):   # the 96-thread FP64 characteristic kernel differs
             np.testing.assert_array_equal(outs[96], outs[128])
 
