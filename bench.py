@@ -55,12 +55,12 @@ FP64_OPS_PER_CELL_STAGE = 3351.0
 FP64_STAGE_DRAM_BYTES = 523.6e6 + 708.3e6
 # FP64 pipe utilisation of the same launch (% of peak sustained, active cycles)
 FP64_PIPE_UTIL_NCU = 0.843
-# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (928 per
-# reconstructed cell less 2.9 % ring redundancy at three blocks per SM), FP32 flops, and the
-# launch's DRAM bytes
+# FP32-bulk kernel (same workload, ncu): FP64 arithmetic operations per cell-stage (923 per
+# reconstructed cell in its default geometry -- 192-thread blocks, 11 bands of 187 columns in
+# 27 row chunks -- less 2.3 % ring redundancy), FP32 flops, and the launch's DRAM bytes
 FP32BULK_FP64_OPS_PER_CELL_STAGE = 902.0
 FP32BULK_FP32_FLOPS_PER_CELL_STAGE = 3971.0
-FP32BULK_STAGE_DRAM_BYTES = 460.9e6 + 1051.2e6
+FP32BULK_STAGE_DRAM_BYTES = 462.6e6 + 1068.4e6
 ALGO_BYTES_PER_CELL_STAGE = 277.3   # 12 values read + 12 written (+8 V-hat, stage mean), FP64
 
 
