@@ -75,7 +75,8 @@ def test_single_solve_covers_the_grid_in_one_wave(geo):
     for _ in range(300):
         nx, ny = (int(v) for v in rng.integers(1, 5000, size=2))
         slots = int(rng.choice([152, 304, 456, 608]))
-        cases.append((nx, ny, 128, slots, 0, 0, int(rng.integers(0, 2))))
+        bw = int(rng.choice([64, 96, 128, 192]))
+        cases.append((nx, ny, bw, slots, 0, 0, int(rng.integers(0, 2))))
     cases += [(1, 1, 128, 304, 0, 0, 1), (2, 3, 128, 304, 0, 0, 0), (126, 1, 128, 304, 0, 0, 0),
               (127, 2, 128, 304, 0, 0, 1), (4096, 4096, 128, 304, 0, 0, 1)]
     out = geo(["G " + " ".join(map(str, c)) for c in cases])
@@ -111,6 +112,11 @@ def test_lane_aware_bands(geo):
     # 286 chunks of 158 rows would leave 18 slots empty); 11 x 27 = 297 chunks of 38 rows
     assert out[0][4:] == [149, 303] and out[0][0] * out[0][2] == 286
     assert out[2][4:] == [0, 297] and out[2][0] * out[2][2] == 297
+    # FP32-bulk 2048^2 in 192-thread blocks, two per SM: 11 bands of 187 columns (189 of the 192
+    # lanes) in 27 chunks of 76 rows (segments of 75 band-rows in up to two pieces would not be
+    # 2 % cheaper)
+    (g192,) = geo(["G 2048 2048 192 304 0 0 0"])
+    assert g192 == [11, 187, 27, 76, 0, 297]
     # the lane-aware choice is taken only when it saves lanes
     rng = np.random.default_rng(3)
     nxs = [int(v) for v in rng.integers(1, 6000, size=200)]
