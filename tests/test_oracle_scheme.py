@@ -176,6 +176,34 @@ def test_reflective_wall_equals_mirrored_periodic_domain():
     np.testing.assert_allclose(B[:, :, :, n:], A, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("axis", [0, 1])
+def test_reflective_walls_2d_equal_mirrored_periodic_domain(axis):
+    """2D Euler with reflective walls on the two x sides (axis 0) or the two y sides (axis 1),
+    periodic across the other direction, equals the periodic domain doubled across the wall
+    with mirrored data: the cells in reverse order across the wall, the normal momentum and
+    every component's normal first moment negated (the normal first moment of the normal
+    momentum twice, so kept)."""
+    n = 10
+    bc = [O.BC_PERIODIC] * 4
+    bc[2 * axis] = bc[2 * axis + 1] = O.BC_REFLECTIVE
+    P = O.Problem(dim=2, eq=O.EULER, nx=n, ny=n, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=tuple(bc))
+    U = I.random_state(P.shape, 12 + axis, eq=O.EULER)
+    ax = 3 - axis                                    # array axis of the wall's direction
+    M = np.flip(U, axis=ax).copy()
+    M[:, 1 + axis] *= -1.0
+    M[1 + axis] *= -1.0
+    D = np.concatenate([M, U], axis=ax)
+    lo = dict(x0=-1.0, nx=2 * n, ny=n) if axis == 0 else dict(y0=-1.0, nx=n, ny=2 * n)
+    kw = dict(dim=2, eq=O.EULER, nx=n, ny=n, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
+              bc=(O.BC_PERIODIC,) * 4)
+    kw.update(lo)
+    PD = O.Problem(**kw)
+    A, _, _, _ = O.run(P, U, 0.0, 1e9, max_steps=3)
+    B, _, _, _ = O.run(PD, D, 0.0, 1e9, max_steps=3)
+    Bw = B[:, :, :, n:] if axis == 0 else B[:, :, n:, :]
+    np.testing.assert_allclose(Bw, A, rtol=0, atol=1e-13)
+
+
 # ------------------------------------------------------------------------------------------
 def _euler_flux(u, gam, dim, d):
     """Textbook Euler flux (complex-safe), independent of the oracle."""
