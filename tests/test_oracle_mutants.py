@@ -167,6 +167,24 @@ MUTANTS = [
     # reflective boundary: the y wall's normal momentum average not negated
     ("reflective y normal momentum", "ua[2] = -ua[2]; vx[2] = -vx[2]; vy[2] = -vy[2];",
      "vx[2] = -vx[2]; vy[2] = -vy[2];"),
+    # Sec. 2.2 Step 2: beta of a linear polynomial without its y slope
+    ("2d beta of p1..p4: dropped slope",
+     "beta[m + 1] = cm[m][1] * cm[m][1] + cm[m][2] * cm[m][2];",
+     "beta[m + 1] = cm[m][1] * cm[m][1];"),
+    # Sec. 2.2 Step 3: linear weights that do not sum to one
+    ("2d linear weights", "double lin[5] = {1.0 - 4.0 * glo, glo, glo, glo, glo};",
+     "double lin[5] = {1.0 - 2.0 * glo, glo, glo, glo, glo};"),
+    # Eq. 2.16: the edge integrals by equal weights instead of the Gauss weights
+    ("2d Gauss weights", "const double wg[3] = {5.0 / 18.0, 4.0 / 9.0, 5.0 / 18.0};",
+     "const double wg[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0};"),
+    # Remark 2.2: the eigenvectors taken at a neighbour's average (2D)
+    ("2d eigenvectors at the wrong cell", "if (orc_eigen(P, ua[4], pass, R, L) != 0) {",
+     "if (orc_eigen(P, ua[1], pass, R, L) != 0) {"),
+    # Eq. 2.13: V-hat of U^n overwritten by every stage (1D)
+    ("1d V-hat overwritten", "if (k == 1) Vh[(int64_t)c * n + i] = vho[c];",
+     "Vh[(int64_t)c * n + i] = vho[c];"),
+    # transmissive boundary: the ghost cell copies the second cell instead of the first
+    ("transmissive clamp", "i = (i < 0) ? 0 : n - 1;", "i = (i < 0) ? 1 : n - 2;"),
     # reflective boundary: the mirror about the boundary cell's centre, not its face
     ("reflective mirror index", "i = (i < 0) ? -1 - i : 2 * n - 1 - i;",
      "i = (i < 0) ? -i : 2 * n - 2 - i;"),
