@@ -11,7 +11,8 @@ namespace hw {
 // keeps the 128-thread kernel that forms the coefficients from each pass's projected stencil:
 // its 96-thread counterpart (coefficients once per cell, 111 KB of shared memory per block),
 // faster for a solve alone, shares the SMs worse with the FP32-bulk class's blocks of a mixed
-// stream (the configured served stream: 0.163 instead of 0.171 solves/s).
+// stream (the configured served stream: 0.163 instead of 0.171 solves/s).  The FP32-bulk
+// class's 192-thread blocks, faster for a solve alone, have not been measured here.
 constexpr int kBatchBW = 128;
 inline int batch_bw2d(int, int, int) { return kBatchBW; }
 constexpr int kBatchClasses = 16;  // {2D, 1D} x {advection, Burgers, Euler comp.-wise,
